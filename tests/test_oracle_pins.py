@@ -1,0 +1,390 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test names the passage it checks.  None of them re-types the oracle's
+formula: they compare it with closed forms, textbook identities, values the
+paper prints, invariants, or convergence rates."""
+import numpy as np
+import pytest
+from scipy import integrate
+from scipy.special import i0
+
+from conftest import golden
+from oracle import fcgram
+from oracle import rte
+from rte_inputs import Grid, Optics, Workload, workload_custom, workload_small
+
+
+# ---------------------------------------------------------------- quadrature
+def test_kphi_closed_form_and_paper_value():
+    """Sec. 5: k_Phi = int exp(-cos^2) = 2 pi e^{-1/2} I_0(1/2) (Bessel
+    generating function); the paper prints 4.052876133898710."""
+    closed = 2 * np.pi * np.exp(-0.5) * i0(0.5)
+    assert abs(closed - golden("k_phi")) < 1e-14
+
+
+def test_trapezoid_ordinates_spectral_convergence():
+    """Sec. 4.1, eq. (RTETrapz): trapezoid rule on theta_m = 2 pi m / M is
+    spectrally accurate for the periodic integrand of Sec. 5."""
+    exact = golden("k_phi")
+    errs = []
+    for M in (4, 8, 12, 16, 24):
+        theta, w, xi, eta = rte.ordinates(M)
+        assert np.allclose(xi ** 2 + eta ** 2, 1)
+        errs.append(abs(w * np.exp(-np.cos(theta) ** 2).sum() - exact))
+    # aliasing error ~ 4 pi e^{-1/2} I_{M/2}(1/2): 2.6e-6, 2.9e-9, ~1e-15
+    assert errs[2] < 1e-5 and errs[3] < 1e-8 and errs[4] < 1e-13
+    assert all(errs[k + 1] < errs[k] * 1e-2 for k in range(3))
+
+
+# ---------------------------------------------------------------- window
+def test_window_function_values():
+    """eq. (sourcelabwind): w(0) = 1, w = 0 for |v| >= 1, even, in (0, 1)
+    inside; w(1/2) = exp(2 e^{-2} / (-1/2)) = exp(-4 e^{-2})."""
+    v = np.array([0.0, 0.5, -0.5, 1.0, -1.0, 1.5])
+    w = rte.window(v)
+    assert w[0] == 1.0 and w[3] == 0 and w[4] == 0 and w[5] == 0
+    assert abs(w[1] - np.exp(-4 * np.exp(-2))) < 1e-15 and w[1] == w[2]
+    x = np.linspace(-0.999, 0.999, 2001)
+    wx = rte.window(x)
+    assert np.all(wx > 0) and np.all(wx <= 1)
+    # C-infinity at the support edge: w(0.99) = exp(-200 e^{-1/0.99}) ~ 1e-32
+    assert rte.window(np.array([0.99]))[0] < 1e-30
+
+
+# ---------------------------------------------------------------- phase
+@pytest.mark.parametrize("g", [0.0, 0.5, 0.8, 0.9])
+@pytest.mark.parametrize("exponent", [1.5, 1.0])
+def test_phase_normalisation_symmetry(g, exponent):
+    """Sec. 4.1: the numerical integral of the phase function is one, so every
+    row of P~ (and, P~ being symmetric circulant, every column) sums to 1."""
+    for M in (8, 16, 32):
+        P = rte.phase_matrix(M, g, exponent)
+        assert np.allclose(P.sum(axis=1), 1, atol=1e-14)
+        assert np.allclose(P, P.T, atol=1e-15)
+        assert np.allclose(P, np.roll(np.roll(P, 1, 0), 1, 1), atol=1e-15)
+        if g == 0:
+            assert np.allclose(P, 1.0 / M)
+
+
+def test_phase_2d_hg_is_poisson_kernel():
+    """With the 2D exponent 1 the HG function is the Poisson kernel: its
+    integral is exactly 1 and its k-th Fourier cosine coefficient is g^k, so
+    the eigenvalues of P~ are g^|k| (up to aliasing ~ g^M)."""
+    g = 0.8
+    val, _ = integrate.quad(lambda t: rte.henyey_greenstein(np.cos(t), g, 1.0), 0, 2 * np.pi,
+                            epsabs=1e-13, limit=200)
+    assert abs(val - 1) < 1e-11
+    M = 64
+    ev = np.sort(np.linalg.eigvalsh(rte.phase_matrix(M, g, 1.0)))[::-1]
+    # trapezoid sampling aliases mode k onto k + jM: eigenvalue
+    # sum_j g^|k + jM| / sum_j g^|jM|
+    alias = lambda k: sum(g ** abs(k + j * M) for j in range(-6, 7))
+    lam = np.array([alias(k) / alias(0) for k in range(M)])
+    assert np.allclose(ev, np.sort(lam)[::-1], atol=1e-13)
+    assert abs(lam[1] - g) < 1e-5
+
+
+def test_phase_mean_cosine_sign():
+    """Forward scattering for g > 0: the mean cosine sum_m' P~ cos(theta_m -
+    theta_m') is positive and increases with g (a sign or index slip in the
+    angle difference flips it)."""
+    M = 32
+    th, _, _, _ = rte.ordinates(M)
+    cosd = np.cos(th[:, None] - th[None, :])
+    mc = [(rte.phase_matrix(M, g) * cosd).sum(axis=1)[0] for g in (0.0, 0.3, 0.6, 0.9)]
+    assert abs(mc[0]) < 1e-14 and 0 < mc[1] < mc[2] < mc[3] < 1
+
+
+# ---------------------------------------------------------------- Fresnel
+def test_fresnel_textbook_forms():
+    """Fresnel reflectance in the independent sine/tangent forms:
+    r_s = -sin(i - t)/sin(i + t), r_p = tan(i - t)/tan(i + t); normal
+    incidence ((n1 - n2)/(n1 + n2))^2; total reflection past asin(1/1.4)."""
+    n1, n2 = golden("n_tissue"), 1.0
+    assert abs(rte.fresnel(1.0, n1, n2) - ((n1 - n2) / (n1 + n2)) ** 2) < 1e-15
+    crit = np.arcsin(n2 / n1)
+    for ang in np.linspace(0.05, crit - 0.02, 12):
+        t = np.arcsin(n1 / n2 * np.sin(ang))
+        rs = -np.sin(ang - t) / np.sin(ang + t)
+        rp = np.tan(ang - t) / np.tan(ang + t)
+        assert abs(rte.fresnel(np.cos(ang), n1, n2) - 0.5 * (rs ** 2 + rp ** 2)) < 1e-13
+    for ang in np.linspace(crit + 1e-6, np.pi / 2, 5):
+        assert rte.fresnel(np.cos(ang), n1, n2) == 1.0
+    brewster = np.arctan(n2 / n1)
+    t = np.arcsin(n1 / n2 * np.sin(brewster))
+    rs = -np.sin(brewster - t) / np.sin(brewster + t)
+    assert abs(rte.fresnel(np.cos(brewster), n1, n2) - 0.5 * rs ** 2) < 1e-14
+
+
+# ---------------------------------------------------------------- reflection maps
+def test_reflection_maps_are_specular():
+    """eq. (RTE): theta_r = 2 theta_nu - theta + pi keeps the tangential and
+    flips the normal component of the direction, on every face."""
+    M = 16
+    grid = Grid(9, 7, 0.0, 1.0, 0.0, 0.75, M)
+    bt = rte.boundary_tables(grid, Optics())
+    th, _, xi, eta = rte.ordinates(M)
+    normals = {0: (-1, 0), 1: (1, 0), 2: (0, -1), 3: (0, 1)}
+    for n in range(len(bt.nodes_j)):
+        j, i = bt.nodes_j[n], bt.nodes_i[n]
+        for m in np.nonzero(bt.active[n])[0]:
+            r = bt.refl[n, m]
+            faces = [F for F, ok in ((0, i == 0), (1, i == grid.nx - 1),
+                                     (2, j == 0), (3, j == grid.ny - 1)) if ok]
+            # the governing face: m incoming, r its specular image
+            good = []
+            for F in faces:
+                nu = normals[F]
+                dn_m = xi[m] * nu[0] + eta[m] * nu[1]
+                dn_r = xi[r] * nu[0] + eta[r] * nu[1]
+                dt_m = -xi[m] * nu[1] + eta[m] * nu[0]
+                dt_r = -xi[r] * nu[1] + eta[r] * nu[0]
+                good.append(dn_m < 0 and abs(dn_m + dn_r) < 1e-12 and abs(dt_m - dt_r) < 1e-12)
+            assert any(good)
+    # every incoming ordinate at a non-corner node is active, outgoing never
+    for n in range(len(bt.nodes_j)):
+        j, i = bt.nodes_j[n], bt.nodes_i[n]
+        if i == 0 and 0 < j < grid.ny - 1:
+            assert np.array_equal(bt.active[n], xi > 1e-12)
+
+
+# ---------------------------------------------------------------- FC derivative
+def test_fc_paper_example_sizes_and_accuracy():
+    """Sec. 4.3 worked example: g = 12 + x^2 - e^{x/3} on [0, 6] with 61 points,
+    d = 5, C = 25, E = 4, N_p = 90 = 2 x 3 x 3 x 5; its FC derivative matches
+    2x - e^{x/3}/3."""
+    n = golden("fc_example_points")
+    Q, A = fcgram.load_tables()
+    assert Q.shape[0] == golden("fc_d") and A.shape[0] == golden("fc_example_C")
+    Np = fcgram.continued_length(n)
+    assert Np == golden("fc_example_Np") and Np - n - A.shape[0] == golden("fc_example_E")
+    x = np.linspace(0, 6, n)
+    g = 12 + x ** 2 - np.exp(x / 3)
+    dg = fcgram.fc_derivative(g, x[1] - x[0])
+    assert np.abs(dg - (2 * x - np.exp(x / 3) / 3)).max() < 1e-6
+
+
+def test_fc_high_order_convergence():
+    """Sec. 4.3: high-order accuracy under refinement (observed order > 3.5)
+    for non-periodic smooth functions."""
+    for f, df in ((lambda x: 12 + x ** 2 - np.exp(x / 3), lambda x: 2 * x - np.exp(x / 3) / 3),
+                  (lambda x: np.sin(1.3 * x + 0.4), lambda x: 1.3 * np.cos(1.3 * x + 0.4))):
+        errs = []
+        for n in (41, 81, 161):
+            x = np.linspace(0, 6, n)
+            errs.append(np.abs(fcgram.fc_derivative(f(x), x[1] - x[0]) - df(x)).max())
+        orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+        assert np.all(orders > 3.5), orders
+
+
+def test_fc_reproduces_low_degree_polynomials():
+    """The continuation is built from the Gram basis of degree < d = 5, so
+    polynomials of degree <= 4 are differentiated to table accuracy."""
+    for n in (64, 128):
+        x = np.linspace(0, 1, n)
+        for p in range(5):
+            d = fcgram.fc_derivative(x ** p, x[1] - x[0])
+            exact = p * x ** (p - 1) if p else 0 * x
+            assert np.abs(d - exact).max() < 1e-9 * max(1, np.abs(exact).max())
+
+
+def test_fc_tables_structure():
+    """Gram basis: orthonormal columns, column j a polynomial of degree j
+    (orthogonal to lower monomials); continuations decay to ~0 at the end of
+    the C continuation points; the continued vector of smooth data is smooth
+    (fast decay of its Fourier coefficients)."""
+    Q, A = fcgram.load_tables()
+    d = Q.shape[0]
+    assert np.allclose(Q.T @ Q, np.eye(d), atol=1e-14)
+    z = np.arange(d, dtype=float)
+    V = np.vander(z, d, increasing=True)
+    assert np.allclose(np.tril(Q.T @ V, -1), 0, atol=1e-9)   # P_j _|_ z^k, k < j
+    assert np.abs(A[-3:]).max() < 1e-6 * max(1, np.abs(A).max())
+    x = np.linspace(0, 1, 100)
+    gc = fcgram.fc_extend(np.exp(x) * np.cos(2 * x))
+    spec = np.abs(np.fft.rfft(gc))
+    freq = np.arange(len(spec)) / len(gc)          # cycles per grid spacing
+    # the continuation is band-limited to K / period = 18 / 60 = 0.3 cycles
+    assert spec[freq > 0.35].max() < 1e-9 * spec.max()
+
+
+def test_fc_dense_operator_equals_fft_path():
+    """The dense operator D (column j = derivative of e_j) reproduces the FFT
+    path on arbitrary data (linearity of eqs. RTEFCSum-RTEFCSumder)."""
+    rng = np.random.default_rng(1)
+    for n in (20, 64, 131):
+        h = 0.1
+        D = fcgram.derivative_matrix(n, h)
+        g = rng.standard_normal((3, n))
+        scale = (np.abs(g) @ np.abs(D).T).max()     # rounding scale of the sum
+        assert np.abs(g @ D.T - fcgram.fc_derivative(g, h)).max() < 1e-12 * scale
+
+
+def test_fc_filter_only_touches_top_modes():
+    """eq. (FFilter) with alpha = 2, beta = 55: sigma(k) = exp(-2 |2k/N_p|^110)
+    is 1 to 1e-5 below 90% of Nyquist and e^{-2} at Nyquist."""
+    Np, h = 90, 1.0
+    mult = fcgram.spectral_multiplier(Np, h)
+    k = np.fft.fftfreq(Np, 1 / Np)
+    ideal = 2j * np.pi * k / (Np * h)
+    low = np.abs(2 * k / Np) < 0.9
+    assert np.allclose(mult[low], ideal[low], rtol=1e-5, atol=0)
+    assert mult[Np // 2] == 0                       # Nyquist mode dropped (even N_p)
+    top = Np // 2 - 1
+    assert abs(abs(mult[top]) / abs(ideal[top]) - np.exp(-2 * (2 * top / Np) ** 110)) < 1e-12
+
+
+# ---------------------------------------------------------------- AB4 + mirror box
+def test_ab4_uniform_isotropic_mirror_box_decays_by_principal_root():
+    """Perfect mirror (f = 1), no source, uniform isotropic field: streaming
+    and scattering vanish, L(u) = -a u, and AB4 (eq. RTEAB4) started on its
+    own principal root rho reproduces u^k = rho^k u^0; rho ~ exp(-c a dt)
+    to fifth order in z = -c a dt."""
+    wl = workload_custom(20, 16, 8, 0, 0.05, mua=0.7, mus=30.0, heterogeneous=False)
+    wl.mua = np.full_like(wl.mua, 0.7)
+    S = rte.Solver(wl, fresnel_override=1.0)
+    z = -wl.c * 0.7 * wl.dt
+    chi = [golden("ab4_chi1"), golden("ab4_chi2"), golden("ab4_chi3")]
+    chi0 = 1 - sum(chi)       # consistency of AB4: the coefficients sum to 1
+    assert abs(chi0 - 55 / 24) < 1e-15
+    # rho^4 = rho^3 + z (chi0 rho^3 + chi1 rho^2 + chi2 rho + chi3)
+    roots = np.roots([1, -(1 + z * chi0), -z * chi[0], -z * chi[1], -z * chi[2]])
+    rho = roots[np.argmin(np.abs(roots - 1))].real
+    assert abs(rho - np.exp(z)) < 2 * abs(z) ** 5
+    u0 = np.ones((8, wl.grid.ny, wl.grid.nx))
+    hist = [-0.7 * u0 * rho ** (-k) for k in (1, 2, 3)]
+    out = S.forward([], 40, inflow=lambda t: 0.0, init=(u0, hist, 0.0))
+    assert np.allclose(out["u"], rho ** 40, rtol=1e-9, atol=0)
+
+
+# ---------------------------------------------------------------- manufactured solution
+def _mms(n, M, dt, T, a=0.35, b=20.0):
+    """Sec. 5, eqs. (RTEdisp)/(RTEmansol): u = exp(-(x-t)^2-(y-t)^2-cos^2 theta)
+    on [0,3]^2, g = 0, c = 1, with its volumetric source and Dirichlet inflow."""
+    kphi = golden("k_phi")
+    g = Grid(n, n, 0.0, 3.0, 0.0, 3.0, M)
+    wl = Workload("mms", g, Optics(g=0.0), np.full((n, n), a), np.full((n, n), b), 1.0, dt, 0, [[]], [])
+    S = rte.Solver(wl, fresnel_override=0.0)
+    th = S.theta[:, None, None]
+    X, Y = S.X[None, None, :], S.Y[None, :, None]
+
+    def uex(t):
+        return np.exp(-(X - t) ** 2 - (Y - t) ** 2 - np.cos(th) ** 2)
+
+    def q(t):
+        Xs, Ys = X - t, Y - t
+        return (uex(t) * (2 * Xs + 2 * Ys - 2 * np.cos(th) * Xs - 2 * np.sin(th) * Ys + a + b)
+                - b * kphi / (2 * np.pi) * np.exp(-Xs ** 2 - Ys ** 2))
+
+    hist = [S.L(uex(-k * dt)) + q(-k * dt) for k in (1, 2, 3)]
+    out = S.forward([], int(round(T / dt)), volume_source=q, init=(uex(0.0), hist, 0.0),
+                    inflow=lambda t: uex(t)[:, S.bt.nodes_j, S.bt.nodes_i].T)
+    t = out["t_end"]
+    exact = kphi * np.exp(-(S.X[None, :] - t) ** 2 - (S.Y[:, None] - t) ** 2)
+    return S.fluence(out["u"]), exact
+
+
+def test_mms_spatial_high_order():
+    """Sec. 5: high-order convergence in dx (observed order > 4)."""
+    errs = [np.abs(np.subtract(*_mms(n, 16, 0.001, 0.1))).max() for n in (25, 37, 49)]
+    ratio = np.array([1.5, 49 / 37 * 36 / 48 * 48 / 36])
+    orders = np.log(np.array(errs[:-1]) / np.array(errs[1:])) / np.log([36 / 24, 48 / 36])
+    assert errs[-1] < 2e-6 and np.all(orders > 4), (errs, orders, ratio)
+
+
+def test_mms_angular_spectral():
+    """Sec. 5: spectral convergence in theta (error drops > 10x per +2
+    ordinates)."""
+    errs = [np.abs(np.subtract(*_mms(40, M, 0.002, 0.1))).max() for M in (6, 8, 10)]
+    assert errs[1] < errs[0] / 10 and errs[2] < errs[1] / 10
+
+
+def test_mms_time_fourth_order():
+    """Sec. 4.2/5: AB4 is fourth order in dt (self-convergence on a fixed
+    grid against a fine-dt run)."""
+    ref, _ = _mms(33, 12, 0.0005, 0.32)
+    errs = [np.abs(_mms(33, 12, dt, 0.32)[0] - ref).max() for dt in (0.008, 0.004)]
+    order = np.log2(errs[0] / errs[1])
+    assert 3.7 < order < 4.3, (errs, order)
+
+
+# ---------------------------------------------------------------- symmetry, linearity
+def test_mirror_symmetric_setup_gives_symmetric_fluence():
+    """A homogeneous square with one beam at the bottom-face centre pointing
+    along +y is symmetric under x -> L - x: so is Phi (to rounding)."""
+    wl = workload_small(n_steps=60, dt=0.05)
+    S = rte.Solver(wl)
+    out = S.forward(wl.groups[0], wl.n_steps, wl.detectors, snap_steps=[59])
+    phi = out["fluence"][59]
+    assert phi.max() > 1e-3
+    assert np.abs(phi - phi[:, ::-1]).max() < 1e-12 * phi.max()
+    c = out["curves"]
+    assert np.allclose(c[0], c[1], rtol=1e-10, atol=1e-300)   # the two bottom detectors
+
+
+def test_mss_curves_superpose_delayed_single_beams():
+    """eqs. (RTEsources)/(RTE) are linear in q: the detector curves of a
+    two-beam staggered group equal the sum of the single-beam curves."""
+    wl = workload_custom(24, 20, 8, 120, 0.04, n_groups=2, t_s=1.0, sigma_t=0.4)
+    b1, b2 = wl.groups[0][0], wl.groups[1][0]
+    b2.tau = 0.8
+    S = rte.Solver(wl)
+    c1 = S.forward([b1], 120, wl.detectors)["curves"]
+    c2 = S.forward([b2], 120, wl.detectors)["curves"]
+    c12 = S.forward([b1, b2], 120, wl.detectors)["curves"]
+    assert np.abs(c12).max() > 0
+    assert np.abs(c12 - (c1 + c2)).max() < 1e-9 * np.abs(c12).max()
+
+
+# ---------------------------------------------------------------- detectors
+def test_detector_operator_on_uniform_field():
+    """eq. (OpMed) on u = 1: G_j = [int w(|s|/sigma_d) ds] x
+    [int_{-pi/2}^{pi/2} (1 - f(cos p)) cos p dp] for a detector in the middle
+    of a face (scipy quad for both factors).  The angular integrand has a
+    square-root kink at the critical angle, so the trapezoid error falls like
+    M^{-3/2}: 1.5% at M = 64, 0.2% at M = 256."""
+    from rte_inputs import Detector
+    ang, _ = integrate.quad(lambda p: (1 - rte.fresnel(np.cos(p))) * np.cos(p), -np.pi / 2, np.pi / 2,
+                            points=[-np.arcsin(1 / 1.4), np.arcsin(1 / 1.4)], epsabs=1e-13)
+    sp, _ = integrate.quad(lambda v: rte.window(np.array([v]))[0], -1, 1, epsabs=1e-13)
+    det = [Detector(1.0, 0.0, 0.3), Detector(2.0, 0.9, 0.25)]
+    rel = []
+    for M in (64, 256):
+        n = 161
+        grid = Grid(n, n, 0.0, 2.0, 0.0, 2.0, M)
+        wl = Workload("u1", grid, Optics(), np.zeros((n, n)), np.zeros((n, n)), 0.02, 0.01, 0, [[]], [])
+        S = rte.Solver(wl)
+        ex = S.exitance(np.ones((M, n, n)))
+        G = S.readout([e[:, None] for e in ex], det)[:, 0]
+        rel.append([abs(G[k] / (d.sigma_d * sp * ang) - 1) for k, d in enumerate(det)])
+    rel = np.array(rel)
+    assert np.all(rel[0] < 0.025) and np.all(rel[1] < 0.003)
+    assert np.all(np.log(rel[0] / rel[1]) / np.log(4) > 1.3)
+
+
+# ---------------------------------------------------------------- photon balance
+def test_photon_balance_with_fresnel_boundary():
+    """Integrating eq. (RTE) over theta and Omega (scattering conserves):
+    d/dt int Phi / c = -(net boundary flux) - int a Phi.  Checked over a run
+    with a beam and Fresnel reflection, to discretisation accuracy."""
+    errs = []
+    for n, dt, steps in ((32, 0.04, 500), (48, 0.03, 667)):
+        wl = workload_custom(n, n, 8, steps, dt, L=1.0, mua=0.5, mus=10.0, heterogeneous=False,
+                             t_s=6.0, sigma_t=2.0)
+        S = rte.Solver(wl)
+        out = S.forward(wl.groups[0], steps, keep_states=True)
+        area = S.node_area()
+        _, w, xi, eta = rte.ordinates(8)
+        N = np.array([np.sum(area * S.fluence(u)) / wl.c for u in out["states"]])
+        absn = np.array([np.sum(area * wl.mua * S.fluence(u)) for u in out["states"]])
+        flux = []
+        for u in out["states"]:
+            tot = 0.0
+            for F, (jj, ii, wg) in enumerate(S.bt.face_nodes):
+                tot += np.sum(wg * ((w * S.bt.face_cos[F]) @ u[:, jj, ii]))
+            flux.append(tot)
+        rate = -np.array(flux) - absn
+        lhs = N[-1] - N[0]
+        rhs = np.trapezoid(rate, dx=dt)
+        errs.append(abs(lhs - rhs) / np.abs(N).max())
+    assert max(errs) < 2e-3, errs
