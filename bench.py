@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the FC-DOM RTE solver (one JSON line on rank 0).
+
+One bench step = one forward solve of the tomography workload: a 256 x 256
+grid on [0,4]^2 cm, M = 32 ordinates, 16 single-beam sources (Transport
+Sweep, 16 independent groups), 2000 AB4 steps, 32 detectors, fluence at the
+last step: 16 * 256 * 256 * 32 * 2000 = 67.1e9 cell-ordinate-step updates.
+The metric is updates/s (whole job); the adjoint gradient rate of the
+Multiple-Staggered-Source workload (4 groups of 4 beams, 3000 steps,
+checkpoints every 100) is reported beside it.
+
+--impl reference times the FP64 CPU oracle (the method's reference
+implementation here) on a bounded sample of the same workload.
+Multi-GPU (torchrun): every rank solves the full workload on its own GPU
+(weak scaling, no collective on the data path); the time is the max over
+ranks and the value counts every rank's updates."""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RTE cell·ordinate·step updates/s and adjoint gradients/s vs plain FP32 GPU"
+UNIT = "updates/s"
+WORKLOAD_DESC = ("tomo256_M32: 256x256 grid on [0,4]^2 cm, M=32 ordinates, background "
+                 "mua=0.1 mus=100 /cm with 3 seeded inclusions, g=0.9, n=1.4, 16 single-beam "
+                 "sources (one group each), 2000 AB4 steps at dt=0.04 ps, 32 detectors")
+# SIMT FP32 peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock).
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+# DRAM traffic per launch from an ncu capture, valid only for the kernel
+# source it was taken on (sha256 of csrc/rte_kernels.cu, first 16 hex digits).
+NCU_TRAFFIC = {
+    # ncu --set full on the tomography workload's per-launch size (16 groups x
+    # 256^2 x 32): profiles/fcdom_passes_tomo256_ncu_full.md
+    ("xpass_kernel", "7ec20f8a420c3adc"): 136.062464e6 + 86.956800e6,
+    ("ypass_kernel", "7ec20f8a420c3adc"): 672.236800e6 + 234.185472e6,
+}
+
+
+def kernel_source_hash():
+    with open(os.path.join(ROOT, "paper_2202_09421_gb300", "csrc", "rte_kernels.cu"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--time-steps", type=int, default=2000, help="AB4 steps per solve")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=40)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- oracle timing
+def oracle_rate(n_steps: int, threads: int = 1):
+    """Times the FP64 oracle on one source of the tomography workload for
+    n_steps AB4 steps in a fresh interpreter pinned to `threads` threads."""
+    code = (
+        "import sys,time,json; sys.path.insert(0, %r)\n"
+        "from rte_inputs import workload_tomo256\n"
+        "from oracle.rte import Solver\n"
+        "wl = workload_tomo256(n_steps=%d)\n"
+        "S = Solver(wl)\n"
+        "t = time.perf_counter(); S.forward(wl.groups[0], %d, wl.detectors); t = time.perf_counter() - t\n"
+        "g = wl.grid\n"
+        "print(json.dumps({'seconds': t, 'updates': g.nx * g.ny * g.M * %d}))\n"
+    ) % (ROOT, n_steps, n_steps, n_steps)
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(threads)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         check=True)
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    return r["updates"] / r["seconds"], r["seconds"]
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = args.cpu_sample_steps
+    for _ in range(args.warmup):
+        oracle_rate(max(2, n // 8))
+    rates, secs = [], []
+    for _ in range(args.steps):
+        r, s = oracle_rate(n)
+        rates.append(r)
+        secs.append(s)
+    value = statistics.median(rates)
+    sample = f"1 of 16 sources x {n} AB4 steps of the tomography workload per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.median(secs), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            self.proc.wait()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for k, nm in enumerate(names):
+                    if p[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2202_09421_gb300 import binding as B
+    from paper_2202_09421_gb300.solver import FCDOMSolver
+    from rte_inputs import workload_mss256, workload_tomo256
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    wl = workload_tomo256(n_steps=args.time_steps)
+    g = wl.grid
+    updates = wl.updates
+    a = torch.tensor(wl.mua, dtype=torch.float32, device=dev)
+    b = torch.tensor(wl.mus, dtype=torch.float32, device=dev)
+    solver = FCDOMSolver(g, wl.optics, a, b, wl.c, wl.dt, ckpt_interval=0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def one_step():
+        solver.forward(wl.groups, wl.n_steps, [wl.n_steps - 1])
+        return solver.readout(wl.detectors)
+
+    for _ in range(args.warmup):
+        one_step()
+        flush.fill_(1.0)
+    barrier()
+    launches0 = solver.kernel_launches()
+    B.rte_set_kernel_timing(solver.ctx, True)
+    times = []
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))                  # evict the previous step from L2
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one_step()
+            e1.record(stream)
+            barrier()
+            times.append(e0.elapsed_time(e1))
+    pass_ms, pass_cnt = B.rte_kernel_times(solver.ctx)
+    B.rte_set_kernel_timing(solver.ctx, False)
+    launches = solver.kernel_launches() - launches0
+    ms_step = max_over_ranks(statistics.mean(times))
+    value = updates * world / (ms_step / 1e3)
+
+    # Roofline of the dominant pass (dense FC-operator products on FP32 SIMT).
+    ncell_m = g.nx * g.ny * g.M * len(wl.groups)
+    flops = [ncell_m * (2 * g.nx + 2 * g.M + 5), ncell_m * (2 * g.ny + 12)]
+    names = ["xpass_kernel", "ypass_kernel"]
+    dom = 0 if pass_ms[0] >= pass_ms[1] else 1
+    avg_ms = pass_ms[dom] / max(1, pass_cnt[dom])
+    achieved = flops[dom] / (avg_ms / 1e3) / 1e12
+    traffic = NCU_TRAFFIC.get((names[dom], kernel_source_hash()))
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "traffic": traffic,
+                "kernel": names[dom], "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "pass_ms_per_launch": [pass_ms[0] / max(1, pass_cnt[0]), pass_ms[1] / max(1, pass_cnt[1])],
+                "pass_share": [pass_ms[0] / sum(pass_ms), pass_ms[1] / sum(pass_ms)]}
+
+    # End to end through the public API with host buffers: copy the medium
+    # from pinned host memory, solve, read the detector curves back.
+    ha = torch.tensor(wl.mua, dtype=torch.float32).pin_memory()
+    hb = torch.tensor(wl.mus, dtype=torch.float32).pin_memory()
+    hc = torch.empty((len(wl.groups), len(wl.detectors), wl.n_steps), dtype=torch.float32).pin_memory()
+    e2e_times = []
+    for k in range(max(1, min(args.steps, 2))):
+        flush.fill_(float(k))
+        barrier()
+        t0 = time.perf_counter()
+        a.copy_(ha, non_blocking=True)
+        b.copy_(hb, non_blocking=True)
+        solver.set_medium(a, b)
+        curves = one_step()
+        hc.copy_(curves, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(statistics.mean(e2e_times))
+    e2e = {"value": updates * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": ha.numel() * 4 + hb.numel() * 4, "d2h_bytes_per_step": hc.numel() * 4}
+    solver.close()
+
+    adjoint = None
+    if not args.no_adjoint:
+        wm = workload_mss256(n_steps=3000)
+        tgt = workload_mss256(n_steps=3000, target=True)
+        am = torch.tensor(wm.mua, dtype=torch.float32, device=dev)
+        bm = torch.tensor(wm.mus, dtype=torch.float32, device=dev)
+        st = FCDOMSolver(tgt.grid, tgt.optics, torch.tensor(tgt.mua, dtype=torch.float32, device=dev),
+                         bm, tgt.c, tgt.dt, ckpt_interval=0)
+        st.forward(tgt.groups, tgt.n_steps)
+        measured = st.readout(tgt.detectors)
+        st.close()
+        sa = FCDOMSolver(wm.grid, wm.optics, am, bm, wm.c, wm.dt, ckpt_interval=100)
+        gt = []
+        for k in range(2):
+            flush.fill_(float(k))
+            barrier()
+            t0 = time.perf_counter()
+            sa.forward(wm.groups, wm.n_steps)
+            J, ga, gb = sa.adjoint_gradient(wm.detectors, measured)
+            torch.cuda.synchronize()
+            gt.append(time.perf_counter() - t0)
+        gs = max_over_ranks(gt[-1])
+        adjoint = {"gradients_per_s": world / gs, "seconds_per_gradient": gs,
+                   "workload": "mss256_M32: 256x256, M=32, 4 MSS groups x 4 beams, 3000 steps, "
+                               "checkpoint every 100, 32 detectors",
+                   "update_equivalents_per_gradient": 3 * wm.updates}
+        sa.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, secs = oracle_rate(args.cpu_sample_steps)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"1 of 16 sources x {args.cpu_sample_steps} AB4 steps of the tomography "
+                         f"workload ({secs:.1f} s, FP64 numpy, 1 thread)"}
+
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "form": "plain FP32 SIMT (dense FC operators)",
+                       "updates_per_step": updates * world, "l2": "flushed between timed steps "
+                       "(256 MB write) and state > L2", "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "adjoint": adjoint,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * rte.h - C ABI of the GB300 FC-DOM solver for the 2D time-domain radiative
+ * transfer equation (Gaggioli & Bruno, "Parallel inverse-problem solver for
+ * time-domain optical tomography with perfect parallel scaling").
+ *
+ * Method (paper sections): transport operator and Fresnel boundary problem,
+ * Sec. 2 eqs. (Toper)/(RTE); Henyey-Greenstein phase, eq. (Henyey-
+ * Greeinstein); discrete ordinates with trapezoid weights, Sec. 4.1 eq.
+ * (RTETrapz); Adams-Bashforth 4, Sec. 4.2 eqs. (RTEAB4)/(RTEAB4L); FC-Gram
+ * continuation and filtered spectral derivative, Sec. 4.3 eqs. (RTEFCSum),
+ * (FFilter), (RTEFCSumder); loop order of Algorithm 1; laser beams, eqs.
+ * (RTEsources)/(RTEsources2); detectors, eq. (OpMed); objective, eq. (FObj);
+ * adjoint problem, eq. (AdjointProblem); gradient, eqs. (gradient_fin) and
+ * (FDwin22).
+ *
+ * Conventions shared by every entry point
+ *  - Units: cm and ps.  Grid point (i, j) sits at (xmin + i dx, ymin + j dy),
+ *    i < nx, j < ny; nx and ny count points (N_x + 1 in the paper).
+ *  - Ordinates theta_m = 2 pi m / M, m = 0..M-1 (M even, 8 <= M <= 64,
+ *    M a multiple of 8).
+ *  - Device arrays are FP32, row-major [j][i] (y outer, x inner), owned by
+ *    the caller; the library copies what it keeps.  Host arrays are plain
+ *    structs owned by the caller and read during the call only.
+ *  - Every call is asynchronous on the context's CUDA stream except where
+ *    noted (J_out synchronises).  The library allocates its own device
+ *    scratch (state, history, checkpoints) with cudaMalloc and frees it in
+ *    rte_destroy.
+ *  - Errors are returned as rte_status; nothing is thrown across the ABI.
+ *    After RTE_ERR_CUDA the context should be destroyed.
+ */
+#ifndef RTE_FCDOM_H
+#define RTE_FCDOM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rte_status {
+  RTE_OK = 0,
+  RTE_ERR_INVALID_ARG = 1,  /* bad pointer, size or parameter */
+  RTE_ERR_UNSTABLE_DT = 2,  /* dt outside the estimated AB4 stability region */
+  RTE_ERR_OOM = 3,          /* cudaMalloc failed */
+  RTE_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed */
+  RTE_ERR_TIMEOUT = 5,      /* a bounded device wait ran out */
+  RTE_ERR_STATE = 6,        /* call order violated (e.g. readout before forward) */
+  RTE_ERR_UNSUPPORTED = 7   /* size outside what the kernels support */
+} rte_status;
+
+/* Uniform grid on [xmin, xmax] x [ymin, ymax] (Sec. 4.3, eq. square) and the
+ * number of discrete ordinates M (Sec. 4.1).  Requires 16 <= nx, ny <= 512. */
+typedef struct rte_grid {
+  int nx, ny;
+  double xmin, xmax, ymin, ymax;
+  int M;
+} rte_grid;
+
+/* Optical constants: HG anisotropy g, refractive indices inside (n_in, the
+ * paper's n_Omega) and outside (n_out, n_0), the HG denominator exponent
+ * (1.5 as printed in the paper, 1.0 for the two-dimensional kernel), and the
+ * speed of light in the medium c (cm/ps). */
+typedef struct rte_optics {
+  double g, n_in, n_out, hg_exponent, c;
+} rte_optics;
+
+/* Time step dt (ps); FC filter (alpha, beta) of eq. (FFilter), normally
+ * (2, 55); checkpoint interval in steps for rte_adjoint_gradient (0: no
+ * checkpoints are kept and the adjoint is unavailable); precision selects the
+ * kernel family (RTE_PREC_FP32: plain FP32 SIMT). */
+#define RTE_PREC_FP32 0
+typedef struct rte_params {
+  double dt;
+  double filter_alpha, filter_beta;
+  int ckpt_interval;
+  int precision;
+} rte_params;
+
+/* One laser beam s_k of eq. (RTEsources2): position (x, y) on the boundary,
+ * direction theta (rad), spreads sigma_x (cm) and sigma_theta (rad), temporal
+ * centre t_s and spread sigma_t (ps), delay tau (ps), amplitude; profile 0 is
+ * a Gaussian in time, profile 1 the window w(|t - tau - t_s| / sigma_t) of
+ * eq. (sourcelab). */
+typedef struct rte_beam {
+  double x, y, theta, sigma_x, sigma_theta, t_s, sigma_t, tau, amplitude;
+  int profile;
+} rte_beam;
+
+/* A generalized source q_i of eq. (RTEsources): its beams fire together
+ * (Transport Sweep: one beam; Multiple Staggered Sources: several, with
+ * delays).  Each group is an independent forward solve. */
+typedef struct rte_source_group {
+  const rte_beam* beams;
+  int n_beams;
+} rte_source_group;
+
+/* Detector of eq. (OpMed) at (x, y) on the boundary with window width
+ * sigma_d (cm). */
+typedef struct rte_detector {
+  double x, y, sigma_d;
+} rte_detector;
+
+typedef struct rte_ctx rte_ctx;
+
+/* Creates a context for one medium: builds in FP64 on the host the FC
+ * derivative operators D_x, D_y (Sec. 4.3), the normalised phase matrix
+ * (Sec. 4.1), the Fresnel/reflection tables of eq. (RTE) and the stability
+ * estimate, and copies mua/mus ([ny][nx] device FP32, the paper's a and b).
+ * cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ * dx and dy may differ; each axis gets its own operator.
+ * Errors: INVALID_ARG (null pointers, M odd or not a multiple of 8, sizes
+ * below 16), UNSUPPORTED (nx or ny above 512, M above 64), UNSTABLE_DT, OOM,
+ * CUDA. */
+rte_status rte_init_medium(rte_ctx** ctx, const rte_grid* grid,
+                           const float* mua, const float* mus,
+                           const rte_optics* optics, const rte_params* params,
+                           void* cuda_stream);
+
+/* Replaces the medium of an existing context (same grid); device FP32
+ * [ny][nx].  Re-checks the stability estimate (UNSTABLE_DT). */
+rte_status rte_set_medium(rte_ctx* ctx, const float* mua, const float* mus);
+
+/* Runs n_steps AB4 steps (Algorithm 1) for every group at once, from the
+ * paper's start-up (levels t^1..t^4 zero; step s produces t = (s + 4) dt and
+ * imposes the boundary condition there).  Records the boundary exitance of
+ * every step (input of rte_detector_readout) and, when the context has a
+ * checkpoint interval, the AB4 checkpoints used by rte_adjoint_gradient.
+ * snap_steps (host, n_snaps entries, each < n_steps) selects steps whose
+ * fluence Phi = sum_m w_m u_m (eq. photondensity) is written to fluence_out
+ * (device FP32 [group][snap][ny][nx]); fluence_out may be NULL when
+ * n_snaps == 0.  Errors: INVALID_ARG, OOM, CUDA. */
+rte_status rte_forward(rte_ctx* ctx, const rte_source_group* groups, int n_groups,
+                       int n_steps, const int* snap_steps, int n_snaps,
+                       float* fluence_out);
+
+/* Detector curves of eq. (OpMed) for the last rte_forward: curves_out
+ * (device FP32 [group][det][step]) receives G_j(t = (s + 4) dt) for every
+ * step s, from the recorded exitance (trapezoid rule along each face,
+ * accumulated in FP64).  Detectors may differ between calls.
+ * Errors: INVALID_ARG, STATE (no forward yet), CUDA. */
+rte_status rte_detector_readout(rte_ctx* ctx, const rte_detector* dets, int n_det,
+                                float* curves_out);
+
+/* Objective only: J = sum_i 1/2 sum_j sum_s (G_j - measured)^2 dt (eqs.
+ * FObj/FObjpr, rectangle rule, FP64 on the device) for the last rte_forward,
+ * written to *J_out (host double; synchronises the stream).  measured: device
+ * FP32 [group][det][step].  Errors: INVALID_ARG, STATE, CUDA. */
+rte_status rte_objective(rte_ctx* ctx, const rte_detector* dets, int n_det,
+                         const float* measured, double* J_out);
+
+/* Objective and gradient: J = sum_i 1/2 sum_j sum_s (G_j - measured)^2 dt
+ * (eqs. FObj/FObjpr, rectangle rule) written to *J_out (host double; this
+ * call synchronises the stream), and the continuous-adjoint gradient of
+ * eqs. (AdjointProblem)/(FDwin22) summed over groups, per grid node:
+ * dJ/dmua = -sum lambda u dtheta A_node dt, dJ/dmus = -sum lambda (u - Pu)
+ * dtheta A_node dt (A_node the trapezoid area of the node), device FP32
+ * [ny][nx] each (either may be NULL).  measured: device FP32
+ * [group][det][step] for the last rte_forward's groups and steps.
+ * Forward states are recomputed segment by segment from the checkpoints.
+ * Errors: INVALID_ARG, STATE (no forward, or ckpt_interval == 0), OOM, CUDA. */
+rte_status rte_adjoint_gradient(rte_ctx* ctx, const rte_detector* dets, int n_det,
+                                const float* measured, double* J_out,
+                                float* dJ_dmua, float* dJ_dmus);
+
+/* Copies the current AB4 state of group g (u after the last step, FP32
+ * [ny][nx][M]) into out (device).  Diagnostic; INVALID_ARG, STATE. */
+rte_status rte_get_state(rte_ctx* ctx, int group, float* out);
+
+/* Host-only helpers (no device work; they run without a GPU).
+ * rte_host_fc_operator writes the dense FP64 FC derivative operator of a line
+ * of n points at spacing h (row-major n x n, D[i*n + j] = d(out_i)/d(g_j);
+ * Sec. 4.3 continuation with d = 5, C = 25 and the filtered derivative of
+ * eqs. (RTEFCSum)-(RTEFCSumder)); 16 <= n <= 4096.
+ * rte_host_phase_matrix writes P~[m*M + q] = w p_{m,q} normalised as in
+ * Sec. 4.1.  Errors: INVALID_ARG. */
+rte_status rte_host_fc_operator(int n, double h, double alpha, double beta, double* D_out);
+rte_status rte_host_phase_matrix(int M, double g, double exponent, double* P_out);
+
+/* Per-kernel timing with CUDA events on the context's stream.  While on,
+ * every AB4 step records events around its two passes (x-pass: scattering
+ * and x-derivative; y-pass: y-derivative, AB4, boundary condition,
+ * exitance).  rte_kernel_times synchronises the stream, writes the summed
+ * device time in ms of each pass (ms_out[2]) and the number of timed launches
+ * of each (count_out[2]), and restarts the count.  Errors: INVALID_ARG, CUDA. */
+rte_status rte_set_kernel_timing(rte_ctx* ctx, int on);
+rte_status rte_kernel_times(rte_ctx* ctx, double* ms_out, long long* count_out);
+
+/* Number of kernels this context has launched since creation. */
+long long rte_kernel_launches(const rte_ctx* ctx);
+
+/* Frees the context and its device memory (synchronises its stream). */
+rte_status rte_destroy(rte_ctx* ctx);
+
+/* Static description of a status code. */
+const char* rte_status_string(rte_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTE_FCDOM_H */

@@ -1,0 +1,227 @@
+"""ctypes binding of the C ABI in include/rte.h.  Argument marshalling only:
+every step of the method runs in the CUDA library.  Loading fails loudly when
+the library has not been built (there is no fallback path).
+
+The functions keep the C names (rte_init_medium, rte_forward, ...); tensors
+are passed as device pointers and must be contiguous CUDA float32."""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_longlong, c_void_p
+
+import torch  # loads the shared CUDA runtime the library links against
+
+from .build import LIB
+
+RTE_PREC_FP32 = 0
+
+
+class RteGrid(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("xmin", c_double), ("xmax", c_double),
+                ("ymin", c_double), ("ymax", c_double), ("M", c_int)]
+
+
+class RteOptics(ctypes.Structure):
+    _fields_ = [("g", c_double), ("n_in", c_double), ("n_out", c_double),
+                ("hg_exponent", c_double), ("c", c_double)]
+
+
+class RteParams(ctypes.Structure):
+    _fields_ = [("dt", c_double), ("filter_alpha", c_double), ("filter_beta", c_double),
+                ("ckpt_interval", c_int), ("precision", c_int)]
+
+
+class RteBeam(ctypes.Structure):
+    _fields_ = [("x", c_double), ("y", c_double), ("theta", c_double), ("sigma_x", c_double),
+                ("sigma_theta", c_double), ("t_s", c_double), ("sigma_t", c_double),
+                ("tau", c_double), ("amplitude", c_double), ("profile", c_int)]
+
+
+class RteSourceGroup(ctypes.Structure):
+    _fields_ = [("beams", POINTER(RteBeam)), ("n_beams", c_int)]
+
+
+class RteDetector(ctypes.Structure):
+    _fields_ = [("x", c_double), ("y", c_double), ("sigma_d", c_double)]
+
+
+class RTEError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: status {status} ({rte_status_string(status)})")
+        self.status = status
+
+
+EXPORTS = ("rte_init_medium", "rte_set_medium", "rte_forward", "rte_detector_readout",
+           "rte_objective", "rte_adjoint_gradient", "rte_get_state", "rte_kernel_launches",
+           "rte_destroy", "rte_status_string", "rte_host_fc_operator", "rte_host_phase_matrix",
+           "rte_set_kernel_timing", "rte_kernel_times")
+
+_lib = None
+
+
+def library() -> ctypes.CDLL:
+    """The loaded librte_fcdom.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise RuntimeError(f"CUDA library {LIB} is missing: build it with "
+                           "`python -m paper_2202_09421_gb300.build` (or __graft_entry__.build())")
+    lib = ctypes.CDLL(LIB)
+    P = c_void_p
+    sig = {
+        "rte_init_medium": [POINTER(c_void_p), POINTER(RteGrid), P, P, POINTER(RteOptics),
+                            POINTER(RteParams), P],
+        "rte_set_medium": [P, P, P],
+        "rte_forward": [P, POINTER(RteSourceGroup), c_int, c_int, POINTER(c_int), c_int, P],
+        "rte_detector_readout": [P, POINTER(RteDetector), c_int, P],
+        "rte_objective": [P, POINTER(RteDetector), c_int, P, POINTER(c_double)],
+        "rte_adjoint_gradient": [P, POINTER(RteDetector), c_int, P, POINTER(c_double), P, P],
+        "rte_get_state": [P, c_int, P],
+        "rte_kernel_launches": [P],
+        "rte_destroy": [P],
+        "rte_status_string": [c_int],
+        "rte_host_fc_operator": [c_int, c_double, c_double, c_double, P],
+        "rte_host_phase_matrix": [c_int, c_double, c_double, P],
+        "rte_set_kernel_timing": [P, c_int],
+        "rte_kernel_times": [P, POINTER(c_double), POINTER(c_longlong)],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = c_int
+    lib.rte_kernel_launches.restype = c_longlong
+    lib.rte_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def rte_status_string(status: int) -> str:
+    return library().rte_status_string(int(status)).decode()
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise RTEError(status, where)
+
+
+def _dev_ptr(t: torch.Tensor | None, name: str):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA float32 tensor")
+    return c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream) -> c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return c_void_p(stream.cuda_stream)
+
+
+def make_beams(beams):
+    arr = (RteBeam * max(1, len(beams)))()
+    for k, b in enumerate(beams):
+        arr[k] = RteBeam(b.x, b.y, b.theta, b.sigma_x, b.sigma_theta, b.t_s, b.sigma_t,
+                         getattr(b, "tau", 0.0), getattr(b, "amplitude", 1.0),
+                         int(getattr(b, "profile", 0)))
+    return arr
+
+
+def make_detectors(dets):
+    arr = (RteDetector * len(dets))()
+    for k, d in enumerate(dets):
+        arr[k] = RteDetector(d.x, d.y, d.sigma_d)
+    return arr
+
+
+# ---------------------------------------------------------------- C-named calls
+def rte_init_medium(grid, mua: torch.Tensor, mus: torch.Tensor, optics, params, stream=None):
+    """grid: object with nx, ny, xmin, xmax, ymin, ymax, M; optics: g, n_in,
+    n_out, hg_exponent and c (cm/ps); params: RteParams.  Returns the context
+    handle (c_void_p)."""
+    ctx = c_void_p()
+    g = RteGrid(grid.nx, grid.ny, grid.xmin, grid.xmax, grid.ymin, grid.ymax, grid.M)
+    o = RteOptics(optics.g, optics.n_in, optics.n_out, optics.hg_exponent, optics.c)
+    _check(library().rte_init_medium(ctypes.byref(ctx), ctypes.byref(g), _dev_ptr(mua, "mua"),
+                                     _dev_ptr(mus, "mus"), ctypes.byref(o), ctypes.byref(params),
+                                     _stream_handle(stream)), "rte_init_medium")
+    return ctx
+
+
+def rte_set_medium(ctx, mua, mus):
+    _check(library().rte_set_medium(ctx, _dev_ptr(mua, "mua"), _dev_ptr(mus, "mus")), "rte_set_medium")
+
+
+def rte_forward(ctx, groups, n_steps: int, snap_steps=(), fluence_out=None):
+    """groups: list of lists of beam objects (one list per generalized source)."""
+    beam_arrays = [make_beams(bl) for bl in groups]
+    garr = (RteSourceGroup * len(groups))()
+    for k, bl in enumerate(groups):
+        garr[k] = RteSourceGroup(ctypes.cast(beam_arrays[k], POINTER(RteBeam)), len(bl))
+    snaps = (c_int * max(1, len(snap_steps)))(*snap_steps)
+    _check(library().rte_forward(ctx, garr, len(groups), int(n_steps), snaps, len(snap_steps),
+                                 _dev_ptr(fluence_out, "fluence_out")), "rte_forward")
+
+
+def rte_detector_readout(ctx, dets, curves_out):
+    _check(library().rte_detector_readout(ctx, make_detectors(dets), len(dets),
+                                          _dev_ptr(curves_out, "curves_out")), "rte_detector_readout")
+
+
+def rte_objective(ctx, dets, measured) -> float:
+    J = c_double()
+    _check(library().rte_objective(ctx, make_detectors(dets), len(dets), _dev_ptr(measured, "measured"),
+                                   ctypes.byref(J)), "rte_objective")
+    return J.value
+
+
+def rte_adjoint_gradient(ctx, dets, measured, dJ_dmua=None, dJ_dmus=None) -> float:
+    J = c_double()
+    _check(library().rte_adjoint_gradient(ctx, make_detectors(dets), len(dets),
+                                          _dev_ptr(measured, "measured"), ctypes.byref(J),
+                                          _dev_ptr(dJ_dmua, "dJ_dmua"), _dev_ptr(dJ_dmus, "dJ_dmus")),
+           "rte_adjoint_gradient")
+    return J.value
+
+
+def rte_get_state(ctx, group: int, out):
+    _check(library().rte_get_state(ctx, int(group), _dev_ptr(out, "out")), "rte_get_state")
+
+
+def rte_kernel_launches(ctx) -> int:
+    return int(library().rte_kernel_launches(ctx))
+
+
+def rte_host_fc_operator(n: int, h: float, alpha: float = 2.0, beta: float = 55.0):
+    """Host FP64 FC derivative operator (numpy n x n)."""
+    import numpy as np
+    out = np.zeros((n, n), dtype=np.float64)
+    _check(library().rte_host_fc_operator(n, h, alpha, beta, c_void_p(out.ctypes.data)),
+           "rte_host_fc_operator")
+    return out
+
+
+def rte_host_phase_matrix(M: int, g: float, exponent: float = 1.5):
+    import numpy as np
+    out = np.zeros((M, M), dtype=np.float64)
+    _check(library().rte_host_phase_matrix(M, g, exponent, c_void_p(out.ctypes.data)),
+           "rte_host_phase_matrix")
+    return out
+
+
+def rte_set_kernel_timing(ctx, on: bool):
+    _check(library().rte_set_kernel_timing(ctx, int(bool(on))), "rte_set_kernel_timing")
+
+
+def rte_kernel_times(ctx):
+    """(ms per pass [x, y], launches per pass [x, y]) since the last call."""
+    ms = (c_double * 2)()
+    cnt = (c_longlong * 2)()
+    _check(library().rte_kernel_times(ctx, ms, cnt), "rte_kernel_times")
+    return [ms[0], ms[1]], [cnt[0], cnt[1]]
+
+
+def rte_destroy(ctx):
+    _check(library().rte_destroy(ctx), "rte_destroy")

@@ -1,0 +1,604 @@
+// C ABI of the FC-DOM library (include/rte.h): context, set-up uploads, the
+// time-march driver, detector readout and the checkpointed adjoint gradient.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/rte.h"
+#include "rte_kernels.cuh"
+#include "rte_setup.h"
+
+using rte_setup::kPi;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct rte_ctx {
+  int nx = 0, ny = 0, M = 0;
+  double xmin = 0, xmax = 0, ymin = 0, ymax = 0, dx = 0, dy = 0;
+  rte_optics opt{};
+  rte_params par{};
+  cudaStream_t stream = nullptr;
+  long long launches = 0;
+  double rho_dx = 0, rho_dy = 0;   // spectral-radius estimates of D_x, D_y
+  size_t plane = 0;                // ny * nx * M
+  int ring_len = 0;
+  std::vector<double> ring_x, ring_y, ring_w;
+  // device tables
+  DevBuf DxT, DyT, PT, xi, eta, mua, mus, area;
+  DevBuf face_refl, corner_refl, face_f, corner_f, face_act, corner_act, wexit;
+  // state of the last forward
+  int G = 0, n_steps = -1, kmax = 0;
+  int hl = 0;                      // history rotation index
+  DevBuf U, R, L[3];
+  DevBuf ring, S, A, T;
+  DevBuf ckpt;
+  int n_ckpt = 0;
+  // per-kernel timing (events around every step's two passes)
+  bool timing = false;
+  std::vector<cudaEvent_t> events;   // 3 per timed step
+  size_t n_timed = 0;
+  // adjoint scratch
+  DevBuf MU, RA, LA[3], seg, curves64, resid, partial, Jdev, rho, grad_a, grad_b, Wd, Wn, lohi;
+};
+
+namespace {
+
+rte_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return RTE_OK;
+  if (e == cudaErrorMemoryAllocation) return RTE_ERR_OOM;
+  return RTE_ERR_CUDA;
+}
+
+rte_status ensure(DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return RTE_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  if (bytes == 0) return RTE_OK;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return RTE_ERR_OOM;
+  }
+  b.bytes = bytes;
+  return RTE_OK;
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+template <class T>
+rte_status upload(DevBuf& b, const std::vector<T>& host, cudaStream_t s) {
+  rte_status st = ensure(b, host.size() * sizeof(T));
+  if (st != RTE_OK) return st;
+  if (host.empty()) return RTE_OK;
+  return cuda_status(cudaMemcpyAsync(b.p, host.data(), host.size() * sizeof(T),
+                                     cudaMemcpyHostToDevice, s));
+}
+
+template <class T>
+std::vector<float> to_f32(const std::vector<T>& v) {
+  return std::vector<float>(v.begin(), v.end());
+}
+
+float* F(DevBuf& b) { return static_cast<float*>(b.p); }
+double* D(DevBuf& b) { return static_cast<double*>(b.p); }
+
+#define RTE_TRY(x)                      \
+  do {                                  \
+    rte_status _s = (x);                \
+    if (_s != RTE_OK) return _s;        \
+  } while (0)
+
+// AB4 stability estimate: the transport eigenvalues lie within an ellipse
+// with real semi-axis c dt max(a + b) and imaginary semi-axis
+// c dt sqrt(2) rho(D); it must fit inside the ellipse through AB4's
+// real-axis (0.3) and imaginary-axis (0.43) stability limits.
+rte_status check_dt(rte_ctx* c, const float* mua, const float* mus) {
+  std::vector<float> a(static_cast<size_t>(c->nx) * c->ny), b(a.size());
+  cudaError_t e = cudaMemcpyAsync(a.data(), mua, a.size() * 4, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b.data(), mus, b.size() * 4, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return RTE_ERR_INVALID_ARG;
+  double mx = 0.0;
+  for (size_t k = 0; k < a.size(); ++k) {
+    if (!(a[k] >= 0.f) || !(b[k] >= 0.f) || !std::isfinite(a[k]) || !std::isfinite(b[k]))
+      return RTE_ERR_INVALID_ARG;
+    mx = std::max(mx, static_cast<double>(a[k]) + b[k]);
+  }
+  const double cdt = c->opt.c * c->par.dt;
+  const double z_abs = cdt * mx;
+  const double z_adv = cdt * std::sqrt(2.0) * std::max(c->rho_dx, c->rho_dy);
+  const double e2 = (z_abs / 0.3) * (z_abs / 0.3) + (z_adv / 0.43) * (z_adv / 0.43);
+  return e2 <= 1.0 ? RTE_OK : RTE_ERR_UNSTABLE_DT;
+}
+
+rte_kern::StepArgs step_args(rte_ctx* c, int G) {
+  rte_kern::StepArgs a;
+  a.nx = c->nx; a.ny = c->ny; a.M = c->M; a.G = G; a.plane = c->plane;
+  a.DxT = F(c->DxT); a.DyT = F(c->DyT); a.PT = F(c->PT);
+  a.xi = F(c->xi); a.eta = F(c->eta); a.mua = F(c->mua); a.mus = F(c->mus);
+  a.cdt = static_cast<float>(c->opt.c * c->par.dt);
+  return a;
+}
+
+rte_kern::BoundaryArgs boundary_args(rte_ctx* c) {
+  rte_kern::BoundaryArgs b;
+  b.face_refl = static_cast<const int*>(c->face_refl.p);
+  b.face_f = F(c->face_f);
+  b.face_act = static_cast<const unsigned char*>(c->face_act.p);
+  b.corner_refl = static_cast<const int*>(c->corner_refl.p);
+  b.corner_f = F(c->corner_f);
+  b.corner_act = static_cast<const unsigned char*>(c->corner_act.p);
+  b.wexit = F(c->wexit);
+  b.S = b.A = b.T = nullptr;
+  b.kmax = 0; b.T_len = 0;
+  b.rho = nullptr; b.rho_len = 0;
+  b.ring_out = nullptr; b.ring_steps = 0;
+  return b;
+}
+
+// Per-detector weights on the ring: trapezoid weight x window (with_trap),
+// or the window alone (the pointwise term of the adjoint boundary condition).
+void detector_weights(const rte_ctx* c, const rte_detector* dets, int n_det, bool with_trap,
+                      std::vector<float>& W, std::vector<int>& lohi) {
+  W.assign(static_cast<size_t>(n_det) * c->ring_len, 0.f);
+  lohi.assign(2 * n_det, 0);
+  for (int d = 0; d < n_det; ++d) {
+    int lo = c->ring_len, hi = 0;
+    for (int k = 0; k < c->ring_len; ++k) {
+      const double r = std::hypot(c->ring_x[k] - dets[d].x, c->ring_y[k] - dets[d].y);
+      const double w = rte_setup::window(r / dets[d].sigma_d) * (with_trap ? c->ring_w[k] : 1.0);
+      if (w != 0.0) {
+        W[static_cast<size_t>(d) * c->ring_len + k] = static_cast<float>(w);
+        lo = std::min(lo, k);
+        hi = std::max(hi, k + 1);
+      }
+    }
+    if (lo > hi) lo = hi = 0;
+    lohi[d] = lo;
+    lohi[n_det + d] = hi;
+  }
+}
+
+double temporal(const rte_beam& b, double t) {
+  const double tt = t - b.tau - b.t_s;
+  if (b.profile == 0) return std::exp(-tt * tt / (2.0 * b.sigma_t * b.sigma_t));
+  return rte_setup::window(std::fabs(tt) / b.sigma_t);
+}
+
+double angdist(double a, double b) {
+  double d = std::fmod(std::fabs(a - b), 2.0 * kPi);
+  return std::min(d, 2.0 * kPi - d);
+}
+
+// Runs steps [s_begin, s_end) of the forward march on (U, R, L), starting
+// from whatever state they hold; records checkpoints/exitance/fluence when
+// asked.
+rte_status march(rte_ctx* c, DevBuf& U, DevBuf& R, DevBuf* L, int& hl, int G, int s_begin,
+                 int s_end, const rte_kern::BoundaryArgs& b, bool save_ckpt,
+                 const std::vector<int>& snap_index, float* fluence_out,
+                 std::vector<float*>* seg_out) {
+  const rte_kern::StepArgs a = step_args(c, G);
+  const size_t gbytes = static_cast<size_t>(G) * c->plane * sizeof(float);
+  const int I = c->par.ckpt_interval;
+  for (int s = s_begin; s < s_end; ++s) {
+    float* L1 = F(L[hl]);
+    float* L2 = F(L[(hl + 1) % 3]);
+    float* L3 = F(L[(hl + 2) % 3]);
+    if (save_ckpt && I > 0 && s % I == 0) {
+      char* base = static_cast<char*>(c->ckpt.p) + static_cast<size_t>(s / I) * 4 * gbytes;
+      const void* src[4] = {U.p, L1, L2, L3};
+      for (int q = 0; q < 4; ++q)
+        RTE_TRY(cuda_status(cudaMemcpyAsync(base + q * gbytes, src[q], gbytes,
+                                            cudaMemcpyDeviceToDevice, c->stream)));
+    }
+    cudaEvent_t* ev = nullptr;
+    if (c->timing) {
+      while (c->events.size() < 3 * (c->n_timed + 1)) {
+        cudaEvent_t e;
+        RTE_TRY(cuda_status(cudaEventCreate(&e)));
+        c->events.push_back(e);
+      }
+      ev = &c->events[3 * c->n_timed++];
+    }
+    RTE_TRY(cuda_status(rte_kern::launch_step(a, b, F(U), F(R), L1, L2, L3, s, c->stream,
+                                              &c->launches, ev)));
+    hl = (hl + 2) % 3;
+    if (fluence_out && snap_index[s] >= 0) {
+      const size_t per = static_cast<size_t>(c->nx) * c->ny;
+      const int n_snaps = static_cast<int>(std::count_if(snap_index.begin(), snap_index.end(),
+                                                         [](int v) { return v >= 0; }));
+      RTE_TRY(cuda_status(rte_kern::launch_fluence(
+          F(U), fluence_out + static_cast<size_t>(snap_index[s]) * per, per * n_snaps, c->nx,
+          c->ny, c->M, G, c->plane, static_cast<float>(2.0 * kPi / c->M), c->stream,
+          &c->launches)));
+    }
+    if (seg_out)
+      RTE_TRY(cuda_status(cudaMemcpyAsync((*seg_out)[s - s_begin], U.p, gbytes,
+                                          cudaMemcpyDeviceToDevice, c->stream)));
+  }
+  return RTE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rte_status_string(rte_status s) {
+  switch (s) {
+    case RTE_OK: return "ok";
+    case RTE_ERR_INVALID_ARG: return "invalid argument";
+    case RTE_ERR_UNSTABLE_DT: return "dt outside the estimated AB4 stability region";
+    case RTE_ERR_OOM: return "device memory allocation failed";
+    case RTE_ERR_CUDA: return "CUDA error";
+    case RTE_ERR_TIMEOUT: return "bounded device wait timed out";
+    case RTE_ERR_STATE: return "call order violated";
+    case RTE_ERR_UNSUPPORTED: return "size not supported by the kernels";
+  }
+  return "unknown status";
+}
+
+long long rte_kernel_launches(const rte_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+rte_status rte_set_kernel_timing(rte_ctx* c, int on) {
+  if (!c) return RTE_ERR_INVALID_ARG;
+  c->timing = on != 0;
+  c->n_timed = 0;
+  return RTE_OK;
+}
+
+rte_status rte_kernel_times(rte_ctx* c, double* ms_out, long long* count_out) {
+  if (!c || !ms_out || !count_out) return RTE_ERR_INVALID_ARG;
+  RTE_TRY(cuda_status(cudaStreamSynchronize(c->stream)));
+  double tx = 0.0, ty = 0.0;
+  for (size_t k = 0; k < c->n_timed; ++k) {
+    float a = 0.f, b = 0.f;
+    RTE_TRY(cuda_status(cudaEventElapsedTime(&a, c->events[3 * k], c->events[3 * k + 1])));
+    RTE_TRY(cuda_status(cudaEventElapsedTime(&b, c->events[3 * k + 1], c->events[3 * k + 2])));
+    tx += a;
+    ty += b;
+  }
+  ms_out[0] = tx;
+  ms_out[1] = ty;
+  count_out[0] = count_out[1] = static_cast<long long>(c->n_timed);
+  c->n_timed = 0;
+  return RTE_OK;
+}
+
+rte_status rte_host_fc_operator(int n, double h, double alpha, double beta, double* D_out) {
+  if (n < 16 || n > 4096 || !(h > 0) || !D_out) return RTE_ERR_INVALID_ARG;
+  std::vector<double> Dm;
+  rte_setup::fc_derivative_matrix(n, h, alpha, beta, Dm);
+  std::memcpy(D_out, Dm.data(), Dm.size() * sizeof(double));
+  return RTE_OK;
+}
+
+rte_status rte_host_phase_matrix(int M, double g, double exponent, double* P_out) {
+  if (M < 2 || !P_out || !(std::fabs(g) < 1.0)) return RTE_ERR_INVALID_ARG;
+  std::vector<double> P;
+  rte_setup::phase_matrix(M, g, exponent, P);
+  std::memcpy(P_out, P.data(), P.size() * sizeof(double));
+  return RTE_OK;
+}
+
+rte_status rte_destroy(rte_ctx* c) {
+  if (!c) return RTE_ERR_INVALID_ARG;
+  cudaStreamSynchronize(c->stream);
+  DevBuf* all[] = {&c->DxT, &c->DyT, &c->PT, &c->xi, &c->eta, &c->mua, &c->mus, &c->area,
+                   &c->face_refl, &c->corner_refl, &c->face_f, &c->corner_f, &c->face_act,
+                   &c->corner_act, &c->wexit, &c->U, &c->R, &c->L[0], &c->L[1], &c->L[2],
+                   &c->ring, &c->S, &c->A, &c->T, &c->ckpt, &c->MU, &c->RA, &c->LA[0],
+                   &c->LA[1], &c->LA[2], &c->seg, &c->curves64, &c->resid, &c->partial,
+                   &c->Jdev, &c->rho, &c->grad_a, &c->grad_b, &c->Wd, &c->Wn, &c->lohi};
+  for (DevBuf* b : all) release(*b);
+  for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+  delete c;
+  return RTE_OK;
+}
+
+rte_status rte_set_medium(rte_ctx* c, const float* mua, const float* mus) {
+  if (!c || !mua || !mus) return RTE_ERR_INVALID_ARG;
+  RTE_TRY(check_dt(c, mua, mus));
+  const size_t bytes = static_cast<size_t>(c->nx) * c->ny * sizeof(float);
+  RTE_TRY(ensure(c->mua, bytes));
+  RTE_TRY(ensure(c->mus, bytes));
+  RTE_TRY(cuda_status(cudaMemcpyAsync(c->mua.p, mua, bytes, cudaMemcpyDeviceToDevice, c->stream)));
+  RTE_TRY(cuda_status(cudaMemcpyAsync(c->mus.p, mus, bytes, cudaMemcpyDeviceToDevice, c->stream)));
+  return RTE_OK;
+}
+
+rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, const float* mus,
+                           const rte_optics* o, const rte_params* p, void* stream) {
+  if (!out || !g || !mua || !mus || !o || !p) return RTE_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (g->nx < 16 || g->ny < 16 || g->M < 8 || g->M % 8 != 0) return RTE_ERR_INVALID_ARG;
+  if (g->nx > 512 || g->ny > 512 || g->M > 64) return RTE_ERR_UNSUPPORTED;
+  if (!(g->xmax > g->xmin) || !(g->ymax > g->ymin)) return RTE_ERR_INVALID_ARG;
+  if (!(p->dt > 0) || !(o->c > 0) || !(o->n_in > 0) || !(o->n_out > 0) || std::fabs(o->g) >= 1.0 ||
+      p->ckpt_interval < 0 || p->precision != RTE_PREC_FP32)
+    return RTE_ERR_INVALID_ARG;
+  rte_ctx* c = new (std::nothrow) rte_ctx();
+  if (!c) return RTE_ERR_OOM;
+  c->nx = g->nx; c->ny = g->ny; c->M = g->M;
+  c->xmin = g->xmin; c->xmax = g->xmax; c->ymin = g->ymin; c->ymax = g->ymax;
+  c->dx = (g->xmax - g->xmin) / (g->nx - 1);
+  c->dy = (g->ymax - g->ymin) / (g->ny - 1);
+  c->opt = *o;
+  c->par = *p;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->plane = static_cast<size_t>(g->nx) * g->ny * g->M;
+  c->ring_len = 2 * g->nx + 2 * g->ny;
+  auto fail = [&](rte_status s) { rte_destroy(c); return s; };
+
+  // FC derivative operators (Sec. 4.3), transposed for the kernels.
+  std::vector<double> Dm;
+  const int dims[2] = {g->nx, g->ny};
+  const double hs[2] = {c->dx, c->dy};
+  DevBuf* dst[2] = {&c->DxT, &c->DyT};
+  for (int ax = 0; ax < 2; ++ax) {
+    const int n = dims[ax];
+    rte_setup::fc_derivative_matrix(n, hs[ax], p->filter_alpha, p->filter_beta, Dm);
+    std::vector<float> T(static_cast<size_t>(n) * n);
+    for (int i = 0; i < n; ++i)
+      for (int k = 0; k < n; ++k) T[static_cast<size_t>(k) * n + i] = static_cast<float>(Dm[static_cast<size_t>(i) * n + k]);
+    rte_status s = upload(*dst[ax], T, c->stream);
+    if (s != RTE_OK) return fail(s);
+  }
+  c->rho_dx = rte_setup::fc_spectral_radius(g->nx, c->dx, p->filter_alpha, p->filter_beta);
+  c->rho_dy = rte_setup::fc_spectral_radius(g->ny, c->dy, p->filter_alpha, p->filter_beta);
+
+  // Phase matrix (Sec. 4.1), transposed: PT[q*M + m] = P~[m][q].
+  std::vector<double> P;
+  rte_setup::phase_matrix(g->M, o->g, o->hg_exponent, P);
+  std::vector<float> PTf(P.size());
+  for (int m = 0; m < g->M; ++m)
+    for (int q = 0; q < g->M; ++q) PTf[static_cast<size_t>(q) * g->M + m] = static_cast<float>(P[static_cast<size_t>(m) * g->M + q]);
+  std::vector<float> xi(g->M), eta(g->M);
+  for (int m = 0; m < g->M; ++m) {
+    xi[m] = static_cast<float>(std::cos(2.0 * kPi * m / g->M));
+    eta[m] = static_cast<float>(std::sin(2.0 * kPi * m / g->M));
+  }
+  rte_setup::BoundaryTables bt;
+  rte_setup::boundary_tables(g->M, o->n_in, o->n_out, bt);
+  rte_setup::ring_geometry(g->nx, g->ny, g->xmin, g->xmax, g->ymin, g->ymax, c->ring_x, c->ring_y,
+                           c->ring_w);
+  std::vector<float> area(static_cast<size_t>(g->nx) * g->ny);
+  for (int j = 0; j < g->ny; ++j)
+    for (int i = 0; i < g->nx; ++i) {
+      double wx = (i == 0 || i == g->nx - 1) ? 0.5 * c->dx : c->dx;
+      double wy = (j == 0 || j == g->ny - 1) ? 0.5 * c->dy : c->dy;
+      area[static_cast<size_t>(j) * g->nx + i] = static_cast<float>(wx * wy);
+    }
+  rte_status s = RTE_OK;
+  if (s == RTE_OK) s = upload(c->PT, PTf, c->stream);
+  if (s == RTE_OK) s = upload(c->xi, xi, c->stream);
+  if (s == RTE_OK) s = upload(c->eta, eta, c->stream);
+  if (s == RTE_OK) s = upload(c->area, area, c->stream);
+  if (s == RTE_OK) s = upload(c->face_refl, bt.face_refl, c->stream);
+  if (s == RTE_OK) s = upload(c->corner_refl, bt.corner_refl, c->stream);
+  if (s == RTE_OK) s = upload(c->face_f, to_f32(bt.face_f), c->stream);
+  if (s == RTE_OK) s = upload(c->corner_f, to_f32(bt.corner_f), c->stream);
+  if (s == RTE_OK) s = upload(c->face_act, bt.face_act, c->stream);
+  if (s == RTE_OK) s = upload(c->corner_act, bt.corner_act, c->stream);
+  if (s == RTE_OK) s = upload(c->wexit, to_f32(bt.wexit), c->stream);
+  if (s == RTE_OK) s = rte_set_medium(c, mua, mus);
+  if (s == RTE_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
+  if (s != RTE_OK) return fail(s);
+  *out = c;
+  return RTE_OK;
+}
+
+rte_status rte_forward(rte_ctx* c, const rte_source_group* groups, int n_groups, int n_steps,
+                       const int* snap_steps, int n_snaps, float* fluence_out) {
+  if (!c || !groups || n_groups <= 0 || n_steps <= 0 || n_snaps < 0) return RTE_ERR_INVALID_ARG;
+  if (n_snaps > 0 && (!snap_steps || !fluence_out)) return RTE_ERR_INVALID_ARG;
+  std::vector<int> snap_index(n_steps, -1);
+  for (int k = 0; k < n_snaps; ++k) {
+    if (snap_steps[k] < 0 || snap_steps[k] >= n_steps || snap_index[snap_steps[k]] >= 0)
+      return RTE_ERR_INVALID_ARG;
+    snap_index[snap_steps[k]] = k;
+  }
+  int kmax = 0;
+  for (int g = 0; g < n_groups; ++g) {
+    if (groups[g].n_beams < 0 || (groups[g].n_beams > 0 && !groups[g].beams)) return RTE_ERR_INVALID_ARG;
+    for (int k = 0; k < groups[g].n_beams; ++k) {
+      const rte_beam& bm = groups[g].beams[k];
+      if (!(bm.sigma_x > 0) || !(bm.sigma_theta > 0) || !(bm.sigma_t > 0)) return RTE_ERR_INVALID_ARG;
+    }
+    kmax = std::max(kmax, groups[g].n_beams);
+  }
+  const int G = n_groups;
+  const size_t gbytes = static_cast<size_t>(G) * c->plane * sizeof(float);
+  RTE_TRY(ensure(c->U, gbytes));
+  RTE_TRY(ensure(c->R, gbytes));
+  for (int q = 0; q < 3; ++q) RTE_TRY(ensure(c->L[q], gbytes));
+  RTE_TRY(ensure(c->ring, static_cast<size_t>(G) * n_steps * c->ring_len * sizeof(float)));
+  const int I = c->par.ckpt_interval;
+  c->n_ckpt = I > 0 ? (n_steps + I - 1) / I : 0;
+  if (I > 0) RTE_TRY(ensure(c->ckpt, static_cast<size_t>(c->n_ckpt) * 4 * gbytes));
+
+  // Source factors q = S(node) A(m) T(step) per beam (eq. RTEsources2).
+  const int kk = std::max(kmax, 1);
+  std::vector<float> S(static_cast<size_t>(G) * kk * c->ring_len, 0.f),
+      A(static_cast<size_t>(G) * kk * c->M, 0.f), T(static_cast<size_t>(G) * kk * n_steps, 0.f);
+  for (int g = 0; g < G; ++g)
+    for (int k = 0; k < groups[g].n_beams; ++k) {
+      const rte_beam& bm = groups[g].beams[k];
+      const size_t gk = static_cast<size_t>(g) * kk + k;
+      for (int nd = 0; nd < c->ring_len; ++nd) {
+        const double dx = c->ring_x[nd] - bm.x, dy = c->ring_y[nd] - bm.y;
+        S[gk * c->ring_len + nd] = static_cast<float>(std::exp(-(dx * dx + dy * dy) / (2.0 * bm.sigma_x * bm.sigma_x)));
+      }
+      for (int m = 0; m < c->M; ++m)
+        A[gk * c->M + m] = static_cast<float>(
+            bm.amplitude * rte_setup::window(angdist(2.0 * kPi * m / c->M, bm.theta) / bm.sigma_theta));
+      for (int s = 0; s < n_steps; ++s)
+        T[gk * n_steps + s] = static_cast<float>(temporal(bm, (s + 4) * c->par.dt));
+    }
+  RTE_TRY(upload(c->S, S, c->stream));
+  RTE_TRY(upload(c->A, A, c->stream));
+  RTE_TRY(upload(c->T, T, c->stream));
+  c->kmax = kmax;
+  c->G = G;
+  c->n_steps = n_steps;
+
+  RTE_TRY(cuda_status(cudaMemsetAsync(c->U.p, 0, gbytes, c->stream)));
+  for (int q = 0; q < 3; ++q) RTE_TRY(cuda_status(cudaMemsetAsync(c->L[q].p, 0, gbytes, c->stream)));
+  c->hl = 0;
+  rte_kern::BoundaryArgs b = boundary_args(c);
+  b.S = F(c->S); b.A = F(c->A); b.T = F(c->T); b.kmax = kmax; b.T_len = n_steps;
+  b.ring_out = F(c->ring); b.ring_steps = n_steps;
+  return march(c, c->U, c->R, c->L, c->hl, G, 0, n_steps, b, true, snap_index, fluence_out, nullptr);
+}
+
+rte_status rte_detector_readout(rte_ctx* c, const rte_detector* dets, int n_det, float* curves_out) {
+  if (!c || !dets || n_det <= 0 || !curves_out) return RTE_ERR_INVALID_ARG;
+  if (c->n_steps <= 0) return RTE_ERR_STATE;
+  for (int d = 0; d < n_det; ++d)
+    if (!(dets[d].sigma_d > 0)) return RTE_ERR_INVALID_ARG;
+  std::vector<float> W;
+  std::vector<int> lohi;
+  detector_weights(c, dets, n_det, true, W, lohi);
+  RTE_TRY(upload(c->Wd, W, c->stream));
+  RTE_TRY(upload(c->lohi, lohi, c->stream));
+  const int* lo = static_cast<const int*>(c->lohi.p);
+  return cuda_status(rte_kern::launch_readout(F(c->ring), c->ring_len, c->n_steps, c->G, F(c->Wd), lo,
+                                              lo + n_det, n_det, curves_out, nullptr, c->stream,
+                                              &c->launches));
+}
+
+rte_status rte_get_state(rte_ctx* c, int group, float* out) {
+  if (!c || !out || group < 0) return RTE_ERR_INVALID_ARG;
+  if (c->n_steps <= 0 || group >= c->G) return RTE_ERR_STATE;
+  return cuda_status(cudaMemcpyAsync(out, F(c->U) + static_cast<size_t>(group) * c->plane,
+                                     c->plane * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+}
+
+rte_status rte_objective(rte_ctx* c, const rte_detector* dets, int n_det, const float* measured,
+                         double* J_out) {
+  if (!c || !dets || n_det <= 0 || !measured || !J_out) return RTE_ERR_INVALID_ARG;
+  if (c->n_steps <= 0) return RTE_ERR_STATE;
+  for (int d = 0; d < n_det; ++d)
+    if (!(dets[d].sigma_d > 0)) return RTE_ERR_INVALID_ARG;
+  const size_t ncurve = static_cast<size_t>(c->G) * n_det * c->n_steps;
+  std::vector<float> Wd;
+  std::vector<int> lohi;
+  detector_weights(c, dets, n_det, true, Wd, lohi);
+  RTE_TRY(upload(c->Wd, Wd, c->stream));
+  RTE_TRY(upload(c->lohi, lohi, c->stream));
+  RTE_TRY(ensure(c->curves64, ncurve * sizeof(double)));
+  RTE_TRY(ensure(c->resid, ncurve * sizeof(float)));
+  RTE_TRY(ensure(c->partial, 256 * sizeof(double)));
+  RTE_TRY(ensure(c->Jdev, sizeof(double)));
+  const int* lo = static_cast<const int*>(c->lohi.p);
+  RTE_TRY(cuda_status(rte_kern::launch_readout(F(c->ring), c->ring_len, c->n_steps, c->G, F(c->Wd), lo,
+                                               lo + n_det, n_det, nullptr, D(c->curves64), c->stream,
+                                               &c->launches)));
+  RTE_TRY(cuda_status(rte_kern::launch_objective(D(c->curves64), measured, ncurve, c->par.dt, F(c->resid),
+                                                 D(c->partial), D(c->Jdev), c->stream, &c->launches)));
+  RTE_TRY(cuda_status(cudaMemcpyAsync(J_out, c->Jdev.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream)));
+  return cuda_status(cudaStreamSynchronize(c->stream));
+}
+
+rte_status rte_adjoint_gradient(rte_ctx* c, const rte_detector* dets, int n_det, const float* measured,
+                                double* J_out, float* dJ_dmua, float* dJ_dmus) {
+  if (!c || !dets || n_det <= 0 || !measured || !J_out) return RTE_ERR_INVALID_ARG;
+  if (c->n_steps <= 0 || c->par.ckpt_interval <= 0) return RTE_ERR_STATE;
+  for (int d = 0; d < n_det; ++d)
+    if (!(dets[d].sigma_d > 0)) return RTE_ERR_INVALID_ARG;
+  const int G = c->G, N = c->n_steps, I = c->par.ckpt_interval;
+  const size_t gfloats = static_cast<size_t>(G) * c->plane, gbytes = gfloats * sizeof(float);
+  const size_t ncurve = static_cast<size_t>(G) * n_det * N;
+  const size_t ncell = static_cast<size_t>(c->nx) * c->ny;
+  std::vector<float> Wd, Wn;
+  std::vector<int> lohi, lohi_n;
+  detector_weights(c, dets, n_det, true, Wd, lohi);
+  detector_weights(c, dets, n_det, false, Wn, lohi_n);
+  RTE_TRY(upload(c->Wd, Wd, c->stream));
+  RTE_TRY(upload(c->Wn, Wn, c->stream));
+  RTE_TRY(upload(c->lohi, lohi, c->stream));
+  RTE_TRY(ensure(c->curves64, ncurve * sizeof(double)));
+  RTE_TRY(ensure(c->resid, ncurve * sizeof(float)));
+  RTE_TRY(ensure(c->partial, 256 * sizeof(double)));
+  RTE_TRY(ensure(c->Jdev, sizeof(double)));
+  RTE_TRY(ensure(c->rho, static_cast<size_t>(G) * N * c->ring_len * sizeof(float)));
+  RTE_TRY(ensure(c->grad_a, ncell * sizeof(double)));
+  RTE_TRY(ensure(c->grad_b, ncell * sizeof(double)));
+  RTE_TRY(ensure(c->MU, gbytes));
+  RTE_TRY(ensure(c->RA, gbytes));
+  for (int q = 0; q < 3; ++q) RTE_TRY(ensure(c->LA[q], gbytes));
+  RTE_TRY(ensure(c->seg, static_cast<size_t>(I) * gbytes));
+  const int* lo = static_cast<const int*>(c->lohi.p);
+
+  // Detector curves (FP64), residual and objective (eq. FObj), then the
+  // adjoint boundary data rho = sum_j r_j w(|x - x_j| / sigma_d).
+  RTE_TRY(cuda_status(rte_kern::launch_readout(F(c->ring), c->ring_len, N, G, F(c->Wd), lo, lo + n_det,
+                                               n_det, nullptr, D(c->curves64), c->stream, &c->launches)));
+  RTE_TRY(cuda_status(rte_kern::launch_objective(D(c->curves64), measured, ncurve, c->par.dt, F(c->resid),
+                                                 D(c->partial), D(c->Jdev), c->stream, &c->launches)));
+  RTE_TRY(cuda_status(rte_kern::launch_rho(F(c->resid), F(c->Wn), n_det, c->ring_len, N, G, F(c->rho),
+                                           c->stream, &c->launches)));
+  RTE_TRY(cuda_status(cudaMemsetAsync(c->grad_a.p, 0, ncell * sizeof(double), c->stream)));
+  RTE_TRY(cuda_status(cudaMemsetAsync(c->grad_b.p, 0, ncell * sizeof(double), c->stream)));
+  RTE_TRY(cuda_status(cudaMemsetAsync(c->MU.p, 0, gbytes, c->stream)));
+  for (int q = 0; q < 3; ++q) RTE_TRY(cuda_status(cudaMemsetAsync(c->LA[q].p, 0, gbytes, c->stream)));
+
+  rte_kern::BoundaryArgs bf = boundary_args(c);
+  bf.S = F(c->S); bf.A = F(c->A); bf.T = F(c->T); bf.kmax = c->kmax; bf.T_len = N;
+  rte_kern::BoundaryArgs ba = boundary_args(c);
+  ba.rho = F(c->rho); ba.rho_len = N;
+  const rte_kern::StepArgs sa = step_args(c, G);
+  const double scale = (2.0 * kPi / c->M) * c->par.dt;
+  int hl_adj = 0;
+  std::vector<int> no_snaps(N, -1);
+  // Levels needed: forward steps 0 .. N-2 (the adjoint vanishes at the last).
+  const int last = N - 2;
+  for (int seg = c->n_ckpt - 1; seg >= 0; --seg) {
+    const int s0 = seg * I;
+    const int s_end = std::min(s0 + I, last + 1);
+    if (s0 > last) continue;
+    // Restore the AB4 state of the checkpoint and recompute the segment.
+    const char* base = static_cast<const char*>(c->ckpt.p) + static_cast<size_t>(seg) * 4 * gbytes;
+    RTE_TRY(cuda_status(cudaMemcpyAsync(c->U.p, base, gbytes, cudaMemcpyDeviceToDevice, c->stream)));
+    for (int q = 0; q < 3; ++q)
+      RTE_TRY(cuda_status(cudaMemcpyAsync(c->L[q].p, base + (q + 1) * gbytes, gbytes,
+                                          cudaMemcpyDeviceToDevice, c->stream)));
+    int hl = 0;
+    std::vector<float*> segp(s_end - s0);
+    for (int k = 0; k < s_end - s0; ++k) segp[k] = F(c->seg) + static_cast<size_t>(k) * gfloats;
+    RTE_TRY(march(c, c->U, c->R, c->L, hl, G, s0, s_end, bf, false, no_snaps, nullptr, &segp));
+    // Adjoint steps for levels s_end-1 .. s0 (eq. AdjointProblem, flipped).
+    for (int lvl = s_end - 1; lvl >= s0; --lvl) {
+      float* L1 = F(c->LA[hl_adj]);
+      float* L2 = F(c->LA[(hl_adj + 1) % 3]);
+      float* L3 = F(c->LA[(hl_adj + 2) % 3]);
+      RTE_TRY(cuda_status(rte_kern::launch_step(sa, ba, F(c->MU), F(c->RA), L1, L2, L3, lvl, c->stream,
+                                                &c->launches)));
+      hl_adj = (hl_adj + 2) % 3;
+      RTE_TRY(cuda_status(rte_kern::launch_grad(F(c->MU), segp[lvl - s0], F(c->PT), F(c->area), c->nx,
+                                                c->ny, c->M, G, c->plane, c->plane, scale,
+                                                dJ_dmua ? D(c->grad_a) : nullptr,
+                                                dJ_dmus ? D(c->grad_b) : nullptr, c->stream,
+                                                &c->launches)));
+    }
+  }
+  // The forward state buffers now hold a recomputed state; mark them stale.
+  if (dJ_dmua)
+    RTE_TRY(cuda_status(rte_kern::launch_to_float(D(c->grad_a), dJ_dmua, ncell, c->stream, &c->launches)));
+  if (dJ_dmus)
+    RTE_TRY(cuda_status(rte_kern::launch_to_float(D(c->grad_b), dJ_dmus, ncell, c->stream, &c->launches)));
+  RTE_TRY(cuda_status(cudaMemcpyAsync(J_out, c->Jdev.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream)));
+  return cuda_status(cudaStreamSynchronize(c->stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,501 @@
+// Plain FP32 SIMT kernels of the FC-DOM step (Algorithm 1 loop body).
+//
+// Layout: U[g][j][i][m] (group, y, x, ordinate), FP32, ordinate innermost so
+// that one grid node's M intensities are contiguous (the scattering sum and
+// the boundary reflections are node-local) and both line directions are
+// dense: an x-line tile is rows (j) x all i x all m; a y-line tile is all j x
+// a few columns (i) x all m, contiguous per row.
+//
+// x-pass: for a block of rows, R = b P~u - (a + b) u - xi_m (D_x u)  [one GEMM
+//         D_x (nx x nx) times the rows' (nx x rows*M) slab, plus the node-local
+//         M x M scattering]
+// y-pass: for a block of columns, L^k = R - eta_m (D_y u); AB4 update of
+//         eq. (RTEAB4); boundary condition of eq. (RTE) on Gamma_-; exitance
+//         of eq. (OpMed) on the boundary ring.  U is updated in place; the
+//         new L^k overwrites the oldest history slot.
+#include <cstdint>
+
+#include "rte_kernels.cuh"
+
+namespace rte_kern {
+
+namespace {
+
+constexpr float kAB0 = 55.0f / 24.0f, kAB1 = -59.0f / 24.0f, kAB2 = 37.0f / 24.0f,
+                kAB3 = -9.0f / 24.0f;
+
+__host__ __device__ inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// Output rows of a tile are padded to 32 so that a block (8 x rows/8
+// threads) is a whole number of warps: the epilogue works warp by warp.
+constexpr int kRowPad = 32;
+
+// acc[r][c] += sum_k A[row0 + r][k] * B[k][col0 + c] over the whole K range,
+// with A given transposed in global memory (AT[k * n + row]) and staged in
+// shared memory chunk by chunk; B is the full slab already in shared memory.
+__device__ inline void gemm_rows(const float* __restrict__ AT, int n, int npad, int kpad,
+                                 const float* Bs, float* As, int row0, int col0,
+                                 float acc[kTM][kTN]) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y;
+  for (int k0 = 0; k0 < kpad; k0 += kKC) {
+    __syncthreads();
+    for (int idx = tid; idx < kKC * npad; idx += nthr) {
+      const int k = idx / npad, r = idx - k * npad;
+      const int kk = k0 + k;
+      As[idx] = (kk < n && r < n) ? __ldg(AT + static_cast<size_t>(kk) * n + r) : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kKC; ++k) {
+      const float4 a0 = *reinterpret_cast<const float4*>(As + k * npad + row0);
+      const float4 a1 = *reinterpret_cast<const float4*>(As + k * npad + row0 + 4);
+      const float4 b0 = *reinterpret_cast<const float4*>(Bs + (k0 + k) * kTileCols + col0);
+      const float4 b1 = *reinterpret_cast<const float4*>(Bs + (k0 + k) * kTileCols + col0 + 4);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int r = 0; r < kTM; ++r)
+#pragma unroll
+        for (int c = 0; c < kTN; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(512) xpass_kernel(StepArgs a, const float* __restrict__ U,
+                                                     float* __restrict__ R) {
+  extern __shared__ __align__(16) float smem[];
+  const int n = a.nx, M = a.M;
+  const int npad = round_up(n, kRowPad), kpad = round_up(n, kKC);
+  const int rows_per_tile = kTileCols / M;
+  float* Bs = smem;                                   // [kpad][64]
+  float* As = Bs + kpad * kTileCols;                  // [kKC][npad]
+  float* Ps = As + kKC * npad;                        // [M][M] (P~ transposed)
+  const int g = blockIdx.z;
+  const int j0 = blockIdx.x * rows_per_tile;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y;
+  const float* Ug = U + static_cast<size_t>(g) * a.plane;
+
+  // Stage the rows' slab: Bs[i'][r*M + m] = u[j0 + r][i'][m].
+  for (int idx = tid; idx < kpad * (kTileCols / 4); idx += nthr) {
+    const int k = idx / (kTileCols / 4), c = (idx - k * (kTileCols / 4)) * 4;
+    const int r = c / M, m = c - r * M, j = j0 + r;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k < n && r < rows_per_tile && j < a.ny)
+      v = __ldg(reinterpret_cast<const float4*>(Ug + (static_cast<size_t>(j) * n + k) * M + m));
+    *reinterpret_cast<float4*>(Bs + k * kTileCols + c) = v;
+  }
+  for (int idx = tid; idx < M * M; idx += nthr) Ps[idx] = __ldg(a.PT + idx);
+
+  const int row0 = threadIdx.y * kTM, col0 = threadIdx.x * kTN;
+  float acc[kTM][kTN];
+#pragma unroll
+  for (int r = 0; r < kTM; ++r)
+#pragma unroll
+    for (int c = 0; c < kTN; ++c) acc[r][c] = 0.f;
+  gemm_rows(a.DxT, n, npad, kpad, Bs, As, row0, col0, acc);
+
+  // Epilogue: node-local scattering and absorption, minus xi * d_x u.
+  // Columns past rows_per_tile * M (M not dividing 64) belong to no row of
+  // this tile.
+  const int r = col0 / M, mb = col0 - r * M, j = j0 + r;
+  if (r >= rows_per_tile || j >= a.ny) return;
+  float xi[kTN];
+#pragma unroll
+  for (int t = 0; t < kTN; ++t) xi[t] = __ldg(a.xi + mb + t);
+#pragma unroll
+  for (int ii = 0; ii < kTM; ++ii) {
+    const int i = row0 + ii;
+    if (i >= n) break;
+    const float* ucell = Bs + i * kTileCols + r * M;
+    float s[kTN];
+#pragma unroll
+    for (int t = 0; t < kTN; ++t) s[t] = 0.f;
+    for (int q = 0; q < M; ++q) {
+      const float uq = ucell[q];
+      const float4 p0 = *reinterpret_cast<const float4*>(Ps + q * M + mb);
+      const float4 p1 = *reinterpret_cast<const float4*>(Ps + q * M + mb + 4);
+      s[0] = fmaf(p0.x, uq, s[0]); s[1] = fmaf(p0.y, uq, s[1]);
+      s[2] = fmaf(p0.z, uq, s[2]); s[3] = fmaf(p0.w, uq, s[3]);
+      s[4] = fmaf(p1.x, uq, s[4]); s[5] = fmaf(p1.y, uq, s[5]);
+      s[6] = fmaf(p1.z, uq, s[6]); s[7] = fmaf(p1.w, uq, s[7]);
+    }
+    const float av = __ldg(a.mua + static_cast<size_t>(j) * n + i);
+    const float bv = __ldg(a.mus + static_cast<size_t>(j) * n + i);
+    float out[kTN];
+#pragma unroll
+    for (int t = 0; t < kTN; ++t)
+      out[t] = bv * s[t] - (av + bv) * ucell[mb + t] - xi[t] * acc[ii][t];
+    float* dst = R + static_cast<size_t>(g) * a.plane + (static_cast<size_t>(j) * n + i) * M + mb;
+    reinterpret_cast<float4*>(dst)[0] = make_float4(out[0], out[1], out[2], out[3]);
+    reinterpret_cast<float4*>(dst)[1] = make_float4(out[4], out[5], out[6], out[7]);
+  }
+}
+
+__device__ inline float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(512) ypass_kernel(StepArgs a, BoundaryArgs b, float* __restrict__ U,
+                                                     const float* __restrict__ R,
+                                                     const float* __restrict__ L1,
+                                                     const float* __restrict__ L2,
+                                                     float* __restrict__ L3, int src_step,
+                                                     int ring_step) {
+  extern __shared__ __align__(16) float smem[];
+  const int nx = a.nx, n = a.ny, M = a.M;
+  const int npad = round_up(n, kRowPad), kpad = round_up(n, kKC);
+  const int cols_per_tile = kTileCols / M;
+  float* Bs = smem;                                   // [kpad][64]
+  float* As = Bs + kpad * kTileCols;                  // [kKC][npad]
+  const int g = blockIdx.z;
+  const int i0 = blockIdx.x * cols_per_tile;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y;
+  const size_t goff = static_cast<size_t>(g) * a.plane;
+  float* Ug = U + goff;
+
+  // Stage the columns' slab: Bs[j'][w*M + m] = u[j'][i0 + w][m] (contiguous).
+  const int valid_cols = min(cols_per_tile, nx - i0) * M;
+  for (int idx = tid; idx < kpad * (kTileCols / 4); idx += nthr) {
+    const int k = idx / (kTileCols / 4), c = (idx - k * (kTileCols / 4)) * 4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k < n && c < valid_cols)
+      v = *reinterpret_cast<const float4*>(Ug + (static_cast<size_t>(k) * nx + i0) * M + c);
+    *reinterpret_cast<float4*>(Bs + k * kTileCols + c) = v;
+  }
+
+  const int row0 = threadIdx.y * kTM, col0 = threadIdx.x * kTN;
+  float acc[kTM][kTN];
+#pragma unroll
+  for (int r = 0; r < kTM; ++r)
+#pragma unroll
+    for (int c = 0; c < kTN; ++c) acc[r][c] = 0.f;
+  gemm_rows(a.DyT, n, npad, kpad, Bs, As, row0, col0, acc);
+
+  // AB4 update (eq. RTEAB4) for this thread's outputs.
+  const int w = col0 / M, mb = col0 - w * M, i = i0 + w;
+  const bool col_ok = w < cols_per_tile && i < nx;
+  float eta[kTN];
+#pragma unroll
+  for (int t = 0; t < kTN; ++t) eta[t] = __ldg(a.eta + mb + t);
+#pragma unroll
+  for (int jj = 0; jj < kTM; ++jj) {
+    const int j = row0 + jj;
+    if (!col_ok || j >= n) {
+#pragma unroll
+      for (int t = 0; t < kTN; ++t) acc[jj][t] = 0.f;
+      continue;
+    }
+    const size_t base = goff + (static_cast<size_t>(j) * nx + i) * M + mb;
+    const float4 r0 = *reinterpret_cast<const float4*>(R + base);
+    const float4 r1 = *reinterpret_cast<const float4*>(R + base + 4);
+    const float4 p0 = *reinterpret_cast<const float4*>(L1 + base);
+    const float4 p1 = *reinterpret_cast<const float4*>(L1 + base + 4);
+    const float4 q0 = *reinterpret_cast<const float4*>(L2 + base);
+    const float4 q1 = *reinterpret_cast<const float4*>(L2 + base + 4);
+    const float4 s0 = *reinterpret_cast<const float4*>(L3 + base);
+    const float4 s1 = *reinterpret_cast<const float4*>(L3 + base + 4);
+    const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+    const float l1[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+    const float l2[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+    const float l3[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+    float lk[8];
+#pragma unroll
+    for (int t = 0; t < kTN; ++t) {
+      lk[t] = rv[t] - eta[t] * acc[jj][t];
+      const float incr = kAB0 * lk[t] + kAB1 * l1[t] + kAB2 * l2[t] + kAB3 * l3[t];
+      acc[jj][t] = fmaf(a.cdt, incr, Bs[j * kTileCols + col0 + t]);   // u^{k+1}, pre-BC
+    }
+    reinterpret_cast<float4*>(L3 + base)[0] = make_float4(lk[0], lk[1], lk[2], lk[3]);
+    reinterpret_cast<float4*>(L3 + base)[1] = make_float4(lk[4], lk[5], lk[6], lk[7]);
+  }
+  __syncthreads();   // every thread has read u^k from Bs
+#pragma unroll
+  for (int jj = 0; jj < kTM; ++jj) {
+    const int j = row0 + jj;
+    if (j < kpad) {
+      *reinterpret_cast<float4*>(Bs + j * kTileCols + col0) =
+          make_float4(acc[jj][0], acc[jj][1], acc[jj][2], acc[jj][3]);
+      *reinterpret_cast<float4*>(Bs + j * kTileCols + col0 + 4) =
+          make_float4(acc[jj][4], acc[jj][5], acc[jj][6], acc[jj][7]);
+    }
+  }
+  __syncthreads();
+
+  // Boundary condition (eq. RTE third line) from the pre-BC values in Bs,
+  // store, and the exitance of eq. (OpMed) on boundary nodes.  One warp per
+  // grid node, lanes over ordinates.
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+  const int ncols = min(cols_per_tile, nx - i0);
+  const int ring_len = 2 * n + 2 * nx;
+  for (int cell = warp; cell < n * ncols; cell += nwarps) {
+    const int j = cell / ncols, wc = cell - j * ncols, ic = i0 + wc;
+    const float* pre = Bs + j * kTileCols + wc * M;
+    const bool lf = ic == 0, rt = ic == nx - 1, bt = j == 0, tp = j == n - 1;
+    const bool bnd = lf || rt || bt || tp;
+    float* dst = Ug + (static_cast<size_t>(j) * nx + ic) * M;
+    if (!bnd) {
+      for (int m = lane; m < M; m += 32) dst[m] = pre[m];
+      continue;
+    }
+    const int* refl;
+    const float* fco;
+    const unsigned char* act;
+    if ((lf || rt) && (bt || tp)) {
+      const int c = (rt ? 1 : 0) + (tp ? 2 : 0);
+      refl = b.corner_refl + c * M; fco = b.corner_f + c * M; act = b.corner_act + c * M;
+    } else {
+      const int F = lf ? 0 : rt ? 1 : bt ? 2 : 3;
+      refl = b.face_refl + F * M; fco = b.face_f + F * M; act = b.face_act + F * M;
+    }
+    // ring node used for the source data (x-face index at corners)
+    const int node = lf ? j : rt ? n + j : bt ? 2 * n + ic : 2 * n + nx + ic;
+    float ex_x = 0.f, ex_y = 0.f;
+    for (int m = lane; m < M; m += 32) {
+      float v = pre[m];
+      if (act[m]) {
+        float q = 0.f;
+        for (int k = 0; k < b.kmax; ++k) {
+          const size_t gk = static_cast<size_t>(g) * b.kmax + k;
+          q = fmaf(b.S[gk * ring_len + node] * b.A[gk * M + m], b.T[gk * b.T_len + src_step], q);
+        }
+        if (b.rho)
+          q = fmaf(1.0f - fco[m], b.rho[(static_cast<size_t>(g) * b.rho_len + src_step) * ring_len + node], q);
+        v = fmaf(fco[m], pre[refl[m]], q);
+      }
+      dst[m] = v;
+      if (lf || rt) ex_x = fmaf(b.wexit[(lf ? 0 : 1) * M + m], v, ex_x);
+      if (bt || tp) ex_y = fmaf(b.wexit[(bt ? 2 : 3) * M + m], v, ex_y);
+    }
+    if (b.ring_out && ring_step >= 0) {
+      float* ro = b.ring_out + (static_cast<size_t>(g) * b.ring_steps + ring_step) * ring_len;
+      if (lf || rt) {
+        ex_x = warp_sum(ex_x);
+        if (lane == 0) ro[lf ? j : n + j] = ex_x;
+      }
+      if (bt || tp) {
+        ex_y = warp_sum(ex_y);
+        if (lane == 0) ro[bt ? 2 * n + ic : 2 * n + nx + ic] = ex_y;
+      }
+    }
+  }
+}
+
+size_t pass_smem(int n, int M, bool xpass) {
+  const int npad = round_up(n, kRowPad), kpad = round_up(n, kKC);
+  size_t f = static_cast<size_t>(kpad) * kTileCols + static_cast<size_t>(kKC) * npad;
+  if (xpass) f += static_cast<size_t>(M) * M;
+  return f * sizeof(float);
+}
+
+__global__ void fluence_kernel(const float* __restrict__ U, float* __restrict__ out,
+                               size_t out_gs, int ncell, int M, size_t plane, float w) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int g = blockIdx.y;
+  if (warp >= ncell) return;
+  const float* u = U + static_cast<size_t>(g) * plane + static_cast<size_t>(warp) * M;
+  float s = 0.f;
+  for (int m = lane; m < M; m += 32) s += u[m];
+  s = warp_sum(s);
+  if (lane == 0) out[static_cast<size_t>(g) * out_gs + warp] = w * s;
+}
+
+__global__ void readout_kernel(const float* __restrict__ ring, int ring_len, int n_steps, int G,
+                               const float* __restrict__ Wd, const int* __restrict__ lo,
+                               const int* __restrict__ hi, int n_det, float* curves,
+                               double* curves64) {
+  const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long total = static_cast<long long>(G) * n_det * n_steps;
+  if (idx >= total) return;
+  const int s = static_cast<int>(idx % n_steps);
+  const int d = static_cast<int>((idx / n_steps) % n_det);
+  const int g = static_cast<int>(idx / (static_cast<long long>(n_steps) * n_det));
+  const float* r = ring + (static_cast<size_t>(g) * n_steps + s) * ring_len;
+  double acc = 0.0;
+  for (int k = lo[d]; k < hi[d]; ++k) {
+    const float wv = Wd[static_cast<size_t>(d) * ring_len + k];
+    if (wv != 0.f) acc += static_cast<double>(wv) * static_cast<double>(r[k]);
+  }
+  if (curves) curves[idx] = static_cast<float>(acc);
+  if (curves64) curves64[idx] = acc;
+}
+
+__global__ void objective_partial(const double* __restrict__ c64, const float* __restrict__ meas,
+                                  size_t n, float* __restrict__ resid, double* __restrict__ partial) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (size_t k = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < n;
+       k += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const double r = c64[k] - static_cast<double>(meas[k]);
+    resid[k] = static_cast<float>(r);
+    s += r * r;
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+__global__ void objective_final(const double* __restrict__ partial, int nb, double scale,
+                                double* J) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) s += partial[k];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *J = scale * sh[0];
+}
+
+__global__ void rho_kernel(const float* __restrict__ resid, const float* __restrict__ Wn, int n_det,
+                           int ring_len, int n_steps, int G, float* __restrict__ rho) {
+  const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long total = static_cast<long long>(G) * n_steps * ring_len;
+  if (idx >= total) return;
+  const int node = static_cast<int>(idx % ring_len);
+  const int s = static_cast<int>((idx / ring_len) % n_steps);
+  const int g = static_cast<int>(idx / (static_cast<long long>(ring_len) * n_steps));
+  float acc = 0.f;
+  for (int d = 0; d < n_det; ++d)
+    acc = fmaf(Wn[static_cast<size_t>(d) * ring_len + node],
+               resid[(static_cast<size_t>(g) * n_det + d) * n_steps + s], acc);
+  rho[idx] = acc;
+}
+
+__global__ void grad_kernel(const float* __restrict__ MU, const float* __restrict__ Useg,
+                            const float* __restrict__ PT, const float* __restrict__ area, int ncell,
+                            int M, int G, size_t plane, size_t useg_gs, double scale,
+                            double* __restrict__ grad_a, double* __restrict__ grad_b) {
+  __shared__ float ubuf[8][64];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const long long cell = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (cell >= ncell) return;   // whole warp exits together
+  float sa = 0.f, sb = 0.f;
+  for (int g = 0; g < G; ++g) {
+    const float* u = Useg + static_cast<size_t>(g) * useg_gs + static_cast<size_t>(cell) * M;
+    const float* mu = MU + static_cast<size_t>(g) * plane + static_cast<size_t>(cell) * M;
+    for (int m = lane; m < M; m += 32) ubuf[wl][m] = u[m];
+    __syncwarp();
+    for (int m = lane; m < M; m += 32) {
+      float pu = 0.f;
+      for (int q = 0; q < M; ++q) pu = fmaf(PT[q * M + m], ubuf[wl][q], pu);
+      const float lam = mu[(m + M / 2) % M];
+      sa = fmaf(lam, ubuf[wl][m], sa);
+      sb = fmaf(lam, ubuf[wl][m] - pu, sb);
+    }
+    __syncwarp();
+  }
+  sa = warp_sum(sa);
+  sb = warp_sum(sb);
+  if (lane == 0) {
+    const double k = scale * static_cast<double>(area[cell]);
+    if (grad_a) grad_a[cell] -= k * static_cast<double>(sa);
+    if (grad_b) grad_b[cell] -= k * static_cast<double>(sb);
+  }
+}
+
+__global__ void to_float_kernel(const double* in, float* out, size_t n) {
+  const size_t k = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k < n) out[k] = static_cast<float>(in[k]);
+}
+
+}  // namespace
+
+cudaError_t launch_step(const StepArgs& a, const BoundaryArgs& b, float* U, float* R,
+                        const float* L1, const float* L2, float* L3, int step,
+                        cudaStream_t s, long long* launches, cudaEvent_t* ev) {
+  static bool attr_done = false;
+  const size_t smx = pass_smem(a.nx, a.M, true), smy = pass_smem(a.ny, a.M, false);
+  if (!attr_done) {
+    cudaFuncSetAttribute(xpass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    cudaFuncSetAttribute(ypass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    attr_done = true;
+  }
+  const int per_tile = kTileCols / a.M;
+  // npad / kTM rows of threads: 8 x (multiple of 4) = whole warps.
+  dim3 bx(kTileCols / kTN, round_up(a.nx, kRowPad) / kTM);
+  dim3 gx((a.ny + per_tile - 1) / per_tile, 1, a.G);
+  if (ev) cudaEventRecord(ev[0], s);
+  xpass_kernel<<<gx, bx, smx, s>>>(a, U, R);
+  if (ev) cudaEventRecord(ev[1], s);
+  dim3 by(kTileCols / kTN, round_up(a.ny, kRowPad) / kTM);
+  dim3 gy((a.nx + per_tile - 1) / per_tile, 1, a.G);
+  const int ring_step = b.ring_out ? step : -1;
+  ypass_kernel<<<gy, by, smy, s>>>(a, b, U, R, L1, L2, L3, step, ring_step);
+  if (ev) cudaEventRecord(ev[2], s);
+  if (launches) *launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fluence(const float* U, float* out, size_t out_group_stride, int nx, int ny,
+                           int M, int G, size_t plane, float w, cudaStream_t s,
+                           long long* launches) {
+  const int ncell = nx * ny;
+  dim3 grid((ncell * 32 + 255) / 256, G);
+  fluence_kernel<<<grid, 256, 0, s>>>(U, out, out_group_stride, ncell, M, plane, w);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_readout(const float* ring, int ring_len, int n_steps, int G,
+                           const float* Wd, const int* lo, const int* hi, int n_det,
+                           float* curves, double* curves64, cudaStream_t s,
+                           long long* launches) {
+  const long long total = static_cast<long long>(G) * n_det * n_steps;
+  if (total == 0) return cudaSuccess;
+  readout_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
+      ring, ring_len, n_steps, G, Wd, lo, hi, n_det, curves, curves64);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_objective(const double* curves64, const float* measured, size_t n,
+                             double dt, float* resid, double* partial, double* J_dev,
+                             cudaStream_t s, long long* launches) {
+  const int nb = 256;
+  objective_partial<<<nb, 256, 0, s>>>(curves64, measured, n, resid, partial);
+  objective_final<<<1, 256, 0, s>>>(partial, nb, 0.5 * dt, J_dev);
+  if (launches) *launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rho(const float* resid, const float* Wn, int n_det, int ring_len,
+                       int n_steps, int G, float* rho, cudaStream_t s, long long* launches) {
+  const long long total = static_cast<long long>(G) * n_steps * ring_len;
+  if (total == 0) return cudaSuccess;
+  rho_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(resid, Wn, n_det, ring_len,
+                                                                         n_steps, G, rho);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad(const float* MU, const float* Useg, const float* PT, const float* area,
+                        int nx, int ny, int M, int G, size_t plane, size_t useg_group_stride,
+                        double scale, double* grad_a, double* grad_b, cudaStream_t s,
+                        long long* launches) {
+  const int ncell = nx * ny;
+  grad_kernel<<<(ncell * 32 + 255) / 256, 256, 0, s>>>(MU, Useg, PT, area, ncell, M, G, plane,
+                                                        useg_group_stride, scale, grad_a, grad_b);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_float(const double* in, float* out, size_t n, cudaStream_t s,
+                            long long* launches) {
+  to_float_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(in, out, n);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace rte_kern

@@ -1,0 +1,86 @@
+// Kernel launchers of the FC-DOM step (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace rte_kern {
+
+// Columns of one pass tile: (rows or columns of the grid) x ordinates.
+constexpr int kTileCols = 64;
+constexpr int kTM = 8, kTN = 8, kKC = 16;
+
+// Boundary/source description shared by the y-pass epilogue.
+struct BoundaryArgs {
+  const int* face_refl;             // [4][M]
+  const float* face_f;              // [4][M]
+  const unsigned char* face_act;    // [4][M]
+  const int* corner_refl;           // [4][M]
+  const float* corner_f;
+  const unsigned char* corner_act;
+  const float* wexit;               // [4][M]
+  // beam sources: q = sum_k S[g][k][node] * A[g][k][m] * T[g][k][step]
+  const float* S;                   // [G][kmax][ring]
+  const float* A;                   // [G][kmax][M]
+  const float* T;                   // [G][kmax][T_len]
+  int kmax, T_len;
+  // adjoint injection: q += (1 - f) * rho[g][step][node]
+  const float* rho;                 // [G][rho_len][ring] or null
+  int rho_len;
+  float* ring_out;                  // [G][ring_steps][ring] exitance, or null
+  int ring_steps;
+};
+
+struct StepArgs {
+  int nx, ny, M, G;
+  size_t plane;                     // ny*nx*M floats per group
+  const float* DxT;                 // [nx][nx], DxT[k*nx + i] = D_x[i][k]
+  const float* DyT;
+  const float* PT;                  // [M][M], PT[q*M + m] = P~[m][q]
+  const float* xi;                  // [M]
+  const float* eta;
+  const float* mua;                 // [ny][nx]
+  const float* mus;
+  float cdt;                        // c * dt
+};
+
+// One AB4 step on all groups: x-pass (R = b P u - (a+b) u - xi d_x u), then
+// y-pass (L = R - eta d_y u, AB4 update, boundary condition, exitance).
+// U is updated in place; Lk is written over L3 (the caller rotates the ring).
+// ev (optional, 3 events) is recorded before the x-pass, between the passes
+// and after the y-pass.
+cudaError_t launch_step(const StepArgs& a, const BoundaryArgs& b, float* U, float* R,
+                        const float* L1, const float* L2, float* L3, int step,
+                        cudaStream_t s, long long* launches, cudaEvent_t* ev = nullptr);
+
+// Phi[g][j][i] = w sum_m u_m  (eq. photondensity).
+cudaError_t launch_fluence(const float* U, float* out, size_t out_group_stride, int nx, int ny,
+                           int M, int G, size_t plane, float w, cudaStream_t s,
+                           long long* launches);
+
+// curves[g][d][s] = sum_node Wd[d][node] ring[g][s][node] over the node
+// range [lo[d], hi[d]) in FP64.
+cudaError_t launch_readout(const float* ring, int ring_len, int n_steps, int G,
+                           const float* Wd, const int* lo, const int* hi, int n_det,
+                           float* curves, double* curves64, cudaStream_t s,
+                           long long* launches);
+
+// J = 1/2 sum (curves - measured)^2 dt in FP64 (deterministic two-level
+// reduction into *J_dev); resid = curves - measured.
+cudaError_t launch_objective(const double* curves64, const float* measured, size_t n,
+                             double dt, float* resid, double* partial, double* J_dev,
+                             cudaStream_t s, long long* launches);
+
+// rho[g][s][node] = sum_d Wn[d][node] resid[g][d][s].
+cudaError_t launch_rho(const float* resid, const float* Wn, int n_det, int ring_len,
+                       int n_steps, int G, float* rho, cudaStream_t s, long long* launches);
+
+// grad_a[c] -= k sum_g sum_m lambda_m u_m; grad_b[c] -= k sum_g sum_m
+// lambda_m (u - P u)_m, with lambda_m = mu_{m + M/2}, k = dtheta dt area[c].
+cudaError_t launch_grad(const float* MU, const float* Useg, const float* PT, const float* area,
+                        int nx, int ny, int M, int G, size_t plane, size_t useg_group_stride,
+                        double scale, double* grad_a, double* grad_b, cudaStream_t s,
+                        long long* launches);
+
+cudaError_t launch_to_float(const double* in, float* out, size_t n, cudaStream_t s,
+                            long long* launches);
+
+}  // namespace rte_kern

@@ -1,0 +1,53 @@
+// Host-side FP64 set-up of the FC-DOM operators and boundary tables.
+// Internal to the library; the kernels receive FP32 copies.
+#pragma once
+#include <vector>
+
+namespace rte_setup {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTieTol = 1e-12;
+
+// Smallest N >= n whose prime factors are all <= 5 (Sec. 4.3: E extra zeros).
+int smooth5(int n);
+
+// Dense FC derivative operator D (n x n, row-major D[i*n + j]) of a line of n
+// points at spacing h: continuation with the FC-Gram table (d = 5, C = 25),
+// filtered spectral derivative of eqs. (RTEFCSum)-(RTEFCSumder) with period
+// N_p h, Nyquist mode dropped.  Built as D = (circulant kernel) * (extension).
+void fc_derivative_matrix(int n, double h, double alpha, double beta,
+                          std::vector<double>& D);
+
+// Largest |multiplier| of the filtered periodic derivative on N_p points,
+// the spectral-radius estimate of D used by the stability check.
+double fc_spectral_radius(int n, double h, double alpha, double beta);
+
+// Normalised phase matrix Pt[m*M + m'] = w p_{m,m'} (Sec. 4.1).
+void phase_matrix(int M, double g, double exponent, std::vector<double>& P);
+
+// Unpolarised Fresnel reflectance at incidence cosine |cos_i|, n_in -> n_out.
+double fresnel(double cos_i, double n_in, double n_out);
+
+// Window function of eq. (sourcelabwind).
+double window(double v);
+
+// Boundary tables.  Faces: 0 left (x = xmin), 1 right, 2 bottom (y = ymin),
+// 3 top.  Corners: 0 (left, bottom), 1 (right, bottom), 2 (left, top),
+// 3 (right, top).  For each (face or corner, m): active (a boundary value is
+// imposed), refl (reflected ordinate), f (Fresnel coefficient of the
+// governing face); exitance weight w (1 - f) cos for outgoing ordinates.
+struct BoundaryTables {
+  std::vector<int> face_refl, corner_refl;      // [4*M]
+  std::vector<double> face_f, corner_f;         // [4*M]
+  std::vector<unsigned char> face_act, corner_act;
+  std::vector<double> wexit;                    // [4*M]
+};
+void boundary_tables(int M, double n_in, double n_out, BoundaryTables& bt);
+
+// Ring of boundary nodes: face 0 nodes j = 0..ny-1, then face 1 (j), face 2
+// (i = 0..nx-1), face 3 (i); node positions and trapezoid weights.
+void ring_geometry(int nx, int ny, double xmin, double xmax, double ymin, double ymax,
+                   std::vector<double>& px, std::vector<double>& py,
+                   std::vector<double>& weight);
+
+}  // namespace rte_setup

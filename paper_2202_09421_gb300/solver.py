@@ -1,0 +1,102 @@
+"""Python-side convenience around the C ABI: a solver object holding one
+context, and a torch.autograd.Function whose backward is the library's
+checkpointed adjoint march (Sec. 3.4-3.6).  Marshalling only."""
+from __future__ import annotations
+
+import torch
+
+from . import binding as B
+
+
+class FCDOMSolver:
+    """One medium on one grid.  grid/optics are duck-typed (nx, ny, xmin, xmax,
+    ymin, ymax, M / g, n_in, n_out, hg_exponent); c is the speed of light in
+    the medium (cm/ps)."""
+
+    def __init__(self, grid, optics, mua: torch.Tensor, mus: torch.Tensor, c: float, dt: float,
+                 ckpt_interval: int = 0, filter_alpha: float = 2.0, filter_beta: float = 55.0,
+                 stream=None):
+        self.grid = grid
+        self.device = mua.device
+
+        class _Opt:
+            pass
+        o = _Opt()
+        o.g, o.n_in, o.n_out = optics.g, optics.n_in, optics.n_out
+        o.hg_exponent, o.c = optics.hg_exponent, c
+        params = B.RteParams(dt, filter_alpha, filter_beta, int(ckpt_interval), B.RTE_PREC_FP32)
+        self.ctx = B.rte_init_medium(grid, mua.contiguous(), mus.contiguous(), o, params, stream)
+        self.n_groups = 0
+        self.n_steps = 0
+
+    def set_medium(self, mua, mus):
+        B.rte_set_medium(self.ctx, mua.contiguous(), mus.contiguous())
+
+    def forward(self, groups, n_steps: int, snap_steps=()):
+        g = self.grid
+        fl = None
+        if snap_steps:
+            fl = torch.empty((len(groups), len(snap_steps), g.ny, g.nx), device=self.device,
+                             dtype=torch.float32)
+        B.rte_forward(self.ctx, groups, n_steps, list(snap_steps), fl)
+        self.n_groups, self.n_steps = len(groups), n_steps
+        return fl
+
+    def readout(self, detectors) -> torch.Tensor:
+        out = torch.empty((self.n_groups, len(detectors), self.n_steps), device=self.device,
+                          dtype=torch.float32)
+        B.rte_detector_readout(self.ctx, detectors, out)
+        return out
+
+    def objective(self, detectors, measured) -> float:
+        return B.rte_objective(self.ctx, detectors, measured.contiguous())
+
+    def adjoint_gradient(self, detectors, measured):
+        g = self.grid
+        ga = torch.empty((g.ny, g.nx), device=self.device, dtype=torch.float32)
+        gb = torch.empty_like(ga)
+        J = B.rte_adjoint_gradient(self.ctx, detectors, measured.contiguous(), ga, gb)
+        return J, ga, gb
+
+    def state(self, group: int) -> torch.Tensor:
+        g = self.grid
+        out = torch.empty((g.ny, g.nx, g.M), device=self.device, dtype=torch.float32)
+        B.rte_get_state(self.ctx, group, out)
+        return out
+
+    def kernel_launches(self) -> int:
+        return B.rte_kernel_launches(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            B.rte_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class RTEObjective(torch.autograd.Function):
+    """J(mua, mus) = sum over groups of eq. (FObj) for the given beams and
+    detectors.  forward: rte_forward + rte_objective; backward: the adjoint
+    march of eq. (AdjointProblem) with checkpoint recompute, giving dJ/dmua
+    and dJ/dmus per grid node (eq. FDwin22)."""
+
+    @staticmethod
+    def forward(ctx, mua, mus, measured, solver: FCDOMSolver, groups, n_steps, detectors):
+        solver.set_medium(mua.detach(), mus.detach())
+        solver.forward(groups, n_steps)
+        J = solver.objective(detectors, measured)
+        ctx.solver, ctx.detectors = solver, detectors
+        ctx.save_for_backward(measured)
+        return torch.tensor(J, dtype=torch.float64, device=mua.device)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        (measured,) = ctx.saved_tensors
+        _, ga, gb = ctx.solver.adjoint_gradient(ctx.detectors, measured)
+        scale = gJ.to(torch.float32)
+        return scale * ga, scale * gb, None, None, None, None, None

@@ -1,0 +1,83 @@
+"""GPU parity of the forward FC-DOM march (FP32 CUDA path through the C ABI)
+against the FP64 oracle on the same seeded inputs.
+
+Tolerance: relative L2 of fluence and detector curves <= 1e-5 (FP32 path);
+full states element-wise within 1e-4 of the state's max magnitude."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import gpu_forward, oracle_forward, rel_l2
+from rte_inputs import workload_custom, workload_small, workload_tomo256
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def _compare(wl, label, state=True, tol=TOL):
+    s, fl, curves = gpu_forward(wl)
+    c_ref, f_ref, u_ref = oracle_forward(wl)
+    ec, ef = rel_l2(curves, c_ref), rel_l2(fl, f_ref)
+    print(f"{label}: curves rel L2 {ec:.3e}, fluence rel L2 {ef:.3e}")
+    assert np.abs(c_ref).max() > 0 and np.abs(f_ref).max() > 0
+    assert ec <= tol and ef <= tol, (ec, ef)
+    if state:
+        for g in range(len(wl.groups)):
+            ug = s.state(g).cpu().numpy()                  # [ny][nx][M]
+            uo = np.moveaxis(u_ref[g], 0, -1)              # oracle [M][ny][nx] -> [ny][nx][M]
+            err = np.abs(ug - uo).max() / np.abs(uo).max()
+            print(f"{label}: group {g} state max err / max {err:.3e}")
+            assert err < 1e-4
+    s.close()
+
+
+def test_forward_small64_M16():
+    """64 x 64, M = 16, one bottom-face beam, 200 steps, 8 detectors."""
+    _compare(workload_small(n_steps=200, dt=0.05), "small64")
+
+
+@pytest.mark.parametrize("nx,ny,M,groups", [(37, 53, 8, 3), (16, 16, 8, 1), (45, 29, 24, 2),
+                                            (70, 66, 64, 1)])
+def test_forward_ragged_sizes(nx, ny, M, groups):
+    """Ragged line lengths (not multiples of the tiles), several groups,
+    seeded inclusions, minimum size and the largest M."""
+    wl = workload_custom(nx, ny, M, 80, 0.04, L=1.0, mus=20.0, n_groups=groups, t_s=1.0,
+                         sigma_t=0.4)
+    _compare(wl, f"ragged{nx}x{ny}_M{M}")
+
+
+def test_forward_tomo256_truncated():
+    """The 256 x 256, M = 32 tomography medium (3 inclusions) at full spatial
+    and angular size, one source, 60 steps (the oracle's bounded sample)."""
+    wl = workload_tomo256(n_steps=60)
+    wl.groups = wl.groups[:1]
+    wl.snap_steps = [59]
+    _compare(wl, "tomo256x60", state=False)
+
+
+def test_mss_superposition_on_gpu():
+    """Linearity in the source (eq. RTE): a two-beam staggered group's curves
+    equal the sum of its single-beam runs."""
+    wl = workload_custom(40, 40, 16, 100, 0.04, n_groups=2, t_s=1.0, sigma_t=0.4)
+    b1, b2 = wl.groups[0][0], wl.groups[1][0]
+    b2.tau = 0.8
+    s, _, c = gpu_forward(wl, groups=[[b1], [b2], [b1, b2]], snaps=[])
+    s.close()
+    assert np.abs(c[2]).max() > 0
+    assert rel_l2(c[2], c[0] + c[1]) < 1e-6
+
+
+def test_zero_source_group_stays_zero():
+    """A group without beams (q = 0) keeps u = 0 exactly."""
+    wl = workload_custom(32, 32, 16, 30, 0.04, n_groups=1)
+    s, fl, c = gpu_forward(wl, groups=[[], wl.groups[0]], snaps=[29])
+    assert np.all(c[0] == 0) and np.all(fl[0] == 0) and np.abs(c[1]).max() > 0
+    s.close()
+
+
+def test_kernel_launch_count():
+    """Two kernels per step (x-pass, y-pass) plus one per fluence snapshot."""
+    wl = workload_custom(32, 32, 16, 25, 0.04, n_groups=1)
+    s, _, _ = gpu_forward(wl, snaps=[24])
+    assert s.kernel_launches() == 2 * 25 + 1 + 1    # + readout
+    s.close()

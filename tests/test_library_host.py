@@ -1,0 +1,100 @@
+"""CPU tests of the C-ABI library: it loads, exports every symbol that
+include/rte.h declares, its host FP64 set-up matches the oracle's operators
+(separately written code, same recipe), and argument validation returns
+error codes before any device work."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "rte.h")
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2202_09421_gb300 import build
+    build(force=False)
+    from paper_2202_09421_gb300 import binding
+    binding.library()
+    return binding
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:rte_status|const char\*|long long)\s+(rte_\w+)\(", text, re.M)))
+
+
+def test_header_declares_the_boundary_calls():
+    syms = declared_symbols()
+    for name in ("rte_init_medium", "rte_forward", "rte_adjoint_gradient", "rte_detector_readout",
+                 "rte_destroy", "rte_status_string"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(B):
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\sT\s(rte_\w+)", out))
+    missing = [s for s in declared_symbols() if s not in exported]
+    assert not missing, missing
+    assert set(B.EXPORTS) == set(declared_symbols())
+
+
+@pytest.mark.parametrize("n,h", [(16, 0.1), (61, 0.1), (64, 2 / 63), (256, 4 / 255), (37, 0.03), (512, 4 / 511)])
+def test_host_fc_operator_matches_oracle(B, n, h):
+    """Separately built tables and operator (library: Lagrange-basis normal
+    equations, circulant kernel in closed form; oracle: Gram basis, QR, FFT)
+    agree to ~1e-12 relative."""
+    from oracle import fcgram
+    D = B.rte_host_fc_operator(n, h)
+    Do = fcgram.derivative_matrix(n, h)
+    assert np.abs(D - Do).max() < 1e-12 * np.abs(Do).max()
+
+
+@pytest.mark.parametrize("M,g,e", [(8, 0.0, 1.5), (16, 0.9, 1.5), (32, 0.8, 1.0), (64, 0.9, 1.5)])
+def test_host_phase_matrix_matches_oracle(B, M, g, e):
+    from oracle import rte
+    assert np.abs(B.rte_host_phase_matrix(M, g, e) - rte.phase_matrix(M, g, e)).max() < 1e-14
+
+
+def test_fc_tables_generators_agree():
+    """The library's table header and the oracle's table file come from two
+    independent generators of the same recipe; they agree to FP64 rounding."""
+    from oracle import fcgram
+    Q, A = fcgram.load_tables()
+    txt = open(os.path.join(ROOT, "paper_2202_09421_gb300", "csrc", "fcgram_table.h")).read()
+    body = txt.split("= {", 1)[1]
+    vals = np.array([float(v) for v in re.findall(r"[-+]?\d+\.\d*(?:e[-+]?\d+)?", body)]).reshape(25, 5)
+    comb = A @ Q.T
+    assert np.abs(vals - comb).max() < 1e-14 * np.abs(comb).max()
+
+
+def test_argument_validation_without_device(B):
+    """Bad sizes and pointers are rejected before any CUDA call."""
+    lib = B.library()
+    ctx = ctypes.c_void_p()
+    dummy = ctypes.c_void_p(16)
+    o = B.RteOptics(0.9, 1.4, 1.0, 1.5, 0.0214)
+    p = B.RteParams(0.05, 2.0, 55.0, 0, 0)
+    bad_grids = [B.RteGrid(8, 64, 0, 1, 0, 1, 16),       # nx too small
+                 B.RteGrid(64, 64, 0, 1, 0, 1, 12),      # M not a multiple of 8
+                 B.RteGrid(64, 64, 1, 0, 0, 1, 16)]      # xmax < xmin
+    for g in bad_grids:
+        assert lib.rte_init_medium(ctypes.byref(ctx), ctypes.byref(g), dummy, dummy, ctypes.byref(o),
+                                   ctypes.byref(p), None) == 1
+    big = B.RteGrid(1024, 64, 0, 1, 0, 1, 16)
+    assert lib.rte_init_medium(ctypes.byref(ctx), ctypes.byref(big), dummy, dummy, ctypes.byref(o),
+                               ctypes.byref(p), None) == 7
+    g = B.RteGrid(64, 64, 0, 1, 0, 1, 16)
+    assert lib.rte_init_medium(ctypes.byref(ctx), ctypes.byref(g), None, dummy, ctypes.byref(o),
+                               ctypes.byref(p), None) == 1
+    neg_dt = B.RteParams(-0.1, 2.0, 55.0, 0, 0)
+    assert lib.rte_init_medium(ctypes.byref(ctx), ctypes.byref(g), dummy, dummy, ctypes.byref(o),
+                               ctypes.byref(neg_dt), None) == 1
+    assert lib.rte_forward(None, None, 0, 0, None, 0, None) == 1
+    assert lib.rte_destroy(None) == 1
+    assert B.rte_status_string(2).startswith("dt outside")
