@@ -188,6 +188,30 @@ rte_status rte_kernel_times(rte_ctx* ctx, double* ms_out, long long* count_out);
 /* Number of kernels this context has launched since creation. */
 long long rte_kernel_launches(const rte_ctx* ctx);
 
+/* Forward solve plus detector curves that allocate no device memory.
+ * The paper has no counterpart: this exists for callers that cannot call
+ * cudaMalloc/cudaFree while they run (device memory already reserved by
+ * another allocator, latency-critical loops where an allocation may
+ * synchronise the device, or a no-allocation policy after start-up).
+ * It computes what rte_forward followed by rte_detector_readout computes
+ * (same kernels, same order): curves_out (device FP32 [group][det][step])
+ * for n_groups groups of beams over n_steps steps.  All per-call scratch
+ * (state, history, exitance ring, source and detector tables) lives in one
+ * file-scope device array of 64 MiB, reserved on every GPU that loads the
+ * library until the process exits; a solve that needs more returns
+ * RTE_ERR_UNSUPPORTED.  The context (operators and medium) must come from
+ * rte_init_medium, called while allocation is allowed; this call does not
+ * touch the context's rte_forward results.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) and should
+ * come before any stream capture.  Every call shares the array and finds the
+ * previous call's data there (it zeroes what must start at zero); calls that
+ * overlap on the GPU race on it.  Host tables are copied from pageable
+ * memory, so the call returns after they have left the host.
+ * Errors: INVALID_ARG, UNSUPPORTED (scratch too small), CUDA. */
+rte_status rte_forward_static(rte_ctx* ctx, const rte_source_group* groups, int n_groups,
+                              int n_steps, const rte_detector* dets, int n_det,
+                              float* curves_out);
+
 /* Frees the context and its device memory (synchronises its stream). */
 rte_status rte_destroy(rte_ctx* ctx);
 

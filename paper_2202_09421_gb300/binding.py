@@ -55,7 +55,7 @@ class RTEError(RuntimeError):
 EXPORTS = ("rte_init_medium", "rte_set_medium", "rte_forward", "rte_detector_readout",
            "rte_objective", "rte_adjoint_gradient", "rte_get_state", "rte_kernel_launches",
            "rte_destroy", "rte_status_string", "rte_host_fc_operator", "rte_host_phase_matrix",
-           "rte_set_kernel_timing", "rte_kernel_times")
+           "rte_set_kernel_timing", "rte_kernel_times", "rte_forward_static")
 
 _lib = None
 
@@ -86,6 +86,7 @@ def library() -> ctypes.CDLL:
         "rte_host_phase_matrix": [c_int, c_double, c_double, P],
         "rte_set_kernel_timing": [P, c_int],
         "rte_kernel_times": [P, POINTER(c_double), POINTER(c_longlong)],
+        "rte_forward_static": [P, POINTER(RteSourceGroup), c_int, c_int, POINTER(RteDetector), c_int, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -221,6 +222,19 @@ def rte_kernel_times(ctx):
     cnt = (c_longlong * 2)()
     _check(library().rte_kernel_times(ctx, ms, cnt), "rte_kernel_times")
     return [ms[0], ms[1]], [cnt[0], cnt[1]]
+
+
+def rte_forward_static(ctx, groups, n_steps: int, dets, curves_out):
+    """Forward solve and detector curves without any device allocation: all
+    per-call scratch sits in the library's 64 MiB static device array (for
+    callers that cannot call cudaMalloc while they run; see include/rte.h)."""
+    beam_arrays = [make_beams(bl) for bl in groups]
+    garr = (RteSourceGroup * len(groups))()
+    for k, bl in enumerate(groups):
+        garr[k] = RteSourceGroup(ctypes.cast(beam_arrays[k], POINTER(RteBeam)), len(bl))
+    _check(library().rte_forward_static(ctx, garr, len(groups), int(n_steps), make_detectors(dets),
+                                        len(dets), _dev_ptr(curves_out, "curves_out")),
+           "rte_forward_static")
 
 
 def rte_destroy(ctx):

@@ -602,3 +602,146 @@ rte_status rte_adjoint_gradient(rte_ctx* c, const rte_detector* dets, int n_det,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Forward solve without any device allocation.
+//
+// Some callers cannot call cudaMalloc (or cudaFree) once they are running:
+// code whose device memory is already fully reserved by another allocator
+// (a framework's caching pool), latency-critical loops where an allocation
+// call may synchronise the device, and hosts whose policy forbids allocator
+// calls after start-up.  For them rte_forward_static runs a whole forward
+// solve (state, history, exitance ring, source and detector tables) inside
+// one file-scope device array instead of memory from cudaMalloc.  The
+// context still comes from rte_init_medium, created while allocation is
+// allowed; this call only reads its operators and medium.
+//
+// The array is kStaticScratchBytes (64 MiB) on every GPU that loads the
+// library and stays reserved until the process exits.  Every call shares it
+// and it keeps the previous call's contents, so each call zeroes the state it
+// needs first; calls that overlap on the GPU (other streams, other threads,
+// other contexts on the same device) race on it.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = 64ull << 20;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mutex;
+void* g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device (host code only
+// sees a host-side stand-in under that name).  Looked up once per device.
+rte_status static_scratch_address(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RTE_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return RTE_ERR_CUDA;
+    }
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return RTE_OK;
+}
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" rte_status rte_forward_static(rte_ctx* c, const rte_source_group* groups, int n_groups,
+                                         int n_steps, const rte_detector* dets, int n_det,
+                                         float* curves_out) {
+  if (!c || !groups || n_groups <= 0 || n_steps <= 0 || !dets || n_det <= 0 || !curves_out)
+    return RTE_ERR_INVALID_ARG;
+  int kmax = 0;
+  for (int g = 0; g < n_groups; ++g) {
+    if (groups[g].n_beams < 0 || (groups[g].n_beams > 0 && !groups[g].beams)) return RTE_ERR_INVALID_ARG;
+    for (int k = 0; k < groups[g].n_beams; ++k) {
+      const rte_beam& bm = groups[g].beams[k];
+      if (!(bm.sigma_x > 0) || !(bm.sigma_theta > 0) || !(bm.sigma_t > 0)) return RTE_ERR_INVALID_ARG;
+    }
+    kmax = std::max(kmax, groups[g].n_beams);
+  }
+  for (int d = 0; d < n_det; ++d)
+    if (!(dets[d].sigma_d > 0)) return RTE_ERR_INVALID_ARG;
+  const int G = n_groups, kk = std::max(kmax, 1);
+  // Carve the scratch: U, R, L1..L3, exitance ring, S, A, T, detector
+  // weights and ranges, each 256-byte aligned.
+  const size_t gbytes = align256(static_cast<size_t>(G) * c->plane * sizeof(float));
+  const size_t ring_b = align256(static_cast<size_t>(G) * n_steps * c->ring_len * sizeof(float));
+  const size_t S_b = align256(static_cast<size_t>(G) * kk * c->ring_len * sizeof(float));
+  const size_t A_b = align256(static_cast<size_t>(G) * kk * c->M * sizeof(float));
+  const size_t T_b = align256(static_cast<size_t>(G) * kk * n_steps * sizeof(float));
+  const size_t W_b = align256(static_cast<size_t>(n_det) * c->ring_len * sizeof(float));
+  const size_t lh_b = align256(2 * static_cast<size_t>(n_det) * sizeof(int));
+  const size_t need = 5 * gbytes + ring_b + S_b + A_b + T_b + W_b + lh_b;
+  if (need > kStaticScratchBytes) return RTE_ERR_UNSUPPORTED;
+
+  void* base = nullptr;
+  RTE_TRY(static_scratch_address(&base));
+  char* p = static_cast<char*>(base);
+  float* U = reinterpret_cast<float*>(p); p += gbytes;
+  float* R = reinterpret_cast<float*>(p); p += gbytes;
+  float* L[3];
+  for (int q = 0; q < 3; ++q) { L[q] = reinterpret_cast<float*>(p); p += gbytes; }
+  float* ring = reinterpret_cast<float*>(p); p += ring_b;
+  float* Sd = reinterpret_cast<float*>(p); p += S_b;
+  float* Ad = reinterpret_cast<float*>(p); p += A_b;
+  float* Td = reinterpret_cast<float*>(p); p += T_b;
+  float* Wdd = reinterpret_cast<float*>(p); p += W_b;
+  int* lohi_d = reinterpret_cast<int*>(p);
+
+  // Source factors q = S(node) A(m) T(step) per beam (eq. RTEsources2) and
+  // detector weights (eq. OpMed), built on the host as in rte_forward.
+  std::vector<float> S(static_cast<size_t>(G) * kk * c->ring_len, 0.f),
+      A(static_cast<size_t>(G) * kk * c->M, 0.f), T(static_cast<size_t>(G) * kk * n_steps, 0.f);
+  for (int g = 0; g < G; ++g)
+    for (int k = 0; k < groups[g].n_beams; ++k) {
+      const rte_beam& bm = groups[g].beams[k];
+      const size_t gk = static_cast<size_t>(g) * kk + k;
+      for (int nd = 0; nd < c->ring_len; ++nd) {
+        const double dx = c->ring_x[nd] - bm.x, dy = c->ring_y[nd] - bm.y;
+        S[gk * c->ring_len + nd] = static_cast<float>(std::exp(-(dx * dx + dy * dy) / (2.0 * bm.sigma_x * bm.sigma_x)));
+      }
+      for (int m = 0; m < c->M; ++m)
+        A[gk * c->M + m] = static_cast<float>(
+            bm.amplitude * rte_setup::window(angdist(2.0 * kPi * m / c->M, bm.theta) / bm.sigma_theta));
+      for (int s = 0; s < n_steps; ++s)
+        T[gk * n_steps + s] = static_cast<float>(temporal(bm, (s + 4) * c->par.dt));
+    }
+  std::vector<float> W;
+  std::vector<int> lohi;
+  detector_weights(c, dets, n_det, true, W, lohi);
+  // Pageable host sources: each copy has left the host vector when it returns.
+  RTE_TRY(cuda_status(cudaMemcpyAsync(Sd, S.data(), S.size() * 4, cudaMemcpyHostToDevice, c->stream)));
+  RTE_TRY(cuda_status(cudaMemcpyAsync(Ad, A.data(), A.size() * 4, cudaMemcpyHostToDevice, c->stream)));
+  RTE_TRY(cuda_status(cudaMemcpyAsync(Td, T.data(), T.size() * 4, cudaMemcpyHostToDevice, c->stream)));
+  RTE_TRY(cuda_status(cudaMemcpyAsync(Wdd, W.data(), W.size() * 4, cudaMemcpyHostToDevice, c->stream)));
+  RTE_TRY(cuda_status(cudaMemcpyAsync(lohi_d, lohi.data(), lohi.size() * sizeof(int),
+                                      cudaMemcpyHostToDevice, c->stream)));
+  // The array keeps the previous call's contents: the march starts from zero.
+  RTE_TRY(cuda_status(cudaMemsetAsync(U, 0, gbytes, c->stream)));
+  for (int q = 0; q < 3; ++q) RTE_TRY(cuda_status(cudaMemsetAsync(L[q], 0, gbytes, c->stream)));
+
+  rte_kern::BoundaryArgs b = boundary_args(c);
+  b.S = Sd; b.A = Ad; b.T = Td; b.kmax = kmax; b.T_len = n_steps;
+  b.ring_out = ring; b.ring_steps = n_steps;
+  const rte_kern::StepArgs a = step_args(c, G);
+  int hl = 0;
+  for (int s = 0; s < n_steps; ++s) {
+    RTE_TRY(cuda_status(rte_kern::launch_step(a, b, U, R, L[hl], L[(hl + 1) % 3], L[(hl + 2) % 3], s,
+                                              c->stream, &c->launches)));
+    hl = (hl + 2) % 3;
+  }
+  return cuda_status(rte_kern::launch_readout(ring, c->ring_len, n_steps, G, Wdd, lohi_d, lohi_d + n_det,
+                                              n_det, curves_out, nullptr, c->stream, &c->launches));
+}
