@@ -67,8 +67,17 @@ typedef struct rte_optics {
 /* Time step dt (ps); FC filter (alpha, beta) of eq. (FFilter), normally
  * (2, 55); checkpoint interval in steps for rte_adjoint_gradient (0: no
  * checkpoints are kept and the adjoint is unavailable); precision selects the
- * kernel family (RTE_PREC_FP32: plain FP32 SIMT). */
+ * kernel family of the FC operator products:
+ *   RTE_PREC_FP32   plain FP32 SIMT kernels (any supported size);
+ *   RTE_PREC_TF32X3 tcgen05 tensor cores, split 3xTF32 operands (FP32-level
+ *                   accuracy); requires nx, ny <= 256 and M in {16, 32};
+ *   RTE_PREC_TF32   tcgen05, single TF32 product (reduced precision, same
+ *                   size limits).
+ * The tensor-core forms synchronise the stream at the end of rte_forward and
+ * rte_adjoint_gradient to read their timeout flag (RTE_ERR_TIMEOUT). */
 #define RTE_PREC_FP32 0
+#define RTE_PREC_TF32X3 1
+#define RTE_PREC_TF32 2
 typedef struct rte_params {
   double dt;
   double filter_alpha, filter_beta;

@@ -14,7 +14,9 @@ import torch  # loads the shared CUDA runtime the library links against
 
 from .build import LIB
 
-RTE_PREC_FP32 = 0
+RTE_PREC_FP32 = 0      # plain FP32 SIMT kernels
+RTE_PREC_TF32X3 = 1    # tcgen05, split 3xTF32 operands (FP32-level accuracy)
+RTE_PREC_TF32 = 2      # tcgen05, one TF32 product (reduced precision)
 
 
 class RteGrid(ctypes.Structure):

@@ -31,6 +31,8 @@ struct rte_ctx {
   // device tables
   DevBuf DxT, DyT, PT, xi, eta, mua, mus, area;
   DevBuf face_refl, corner_refl, face_f, corner_f, face_act, corner_act, wexit;
+  DevBuf DxImg, DyImg, PImg;       // split, swizzled operators (tensor-core forms)
+  int tc_mode = 0;                 // 0 SIMT FP32, 1 tcgen05 3xTF32, 2 tcgen05 1xTF32
   // state of the last forward
   int G = 0, n_steps = -1, kmax = 0;
   int hl = 0;                      // history rotation index
@@ -128,6 +130,10 @@ rte_kern::StepArgs step_args(rte_ctx* c, int G) {
   a.DxT = F(c->DxT); a.DyT = F(c->DyT); a.PT = F(c->PT);
   a.xi = F(c->xi); a.eta = F(c->eta); a.mua = F(c->mua); a.mus = F(c->mus);
   a.cdt = static_cast<float>(c->opt.c * c->par.dt);
+  a.tc_mode = c->tc_mode;
+  a.DxImg = F(c->DxImg);
+  a.DyImg = F(c->DyImg);
+  a.PImg = F(c->PImg);
   return a;
 }
 
@@ -230,6 +236,16 @@ rte_status march(rte_ctx* c, DevBuf& U, DevBuf& R, DevBuf* L, int& hl, int G, in
   return RTE_OK;
 }
 
+// The tcgen05 kernels bound every wait and raise a device flag instead of
+// hanging; the tensor-core forms synchronise at the end of a march to read it.
+rte_status tc_check(rte_ctx* c) {
+  if (c->tc_mode == 0) return RTE_OK;
+  RTE_TRY(cuda_status(cudaStreamSynchronize(c->stream)));
+  int flag = 0;
+  RTE_TRY(cuda_status(rte_kern::tc_take_error(&flag)));
+  return flag ? RTE_ERR_TIMEOUT : RTE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -299,7 +315,8 @@ rte_status rte_destroy(rte_ctx* c) {
                    &c->corner_act, &c->wexit, &c->U, &c->R, &c->L[0], &c->L[1], &c->L[2],
                    &c->ring, &c->S, &c->A, &c->T, &c->ckpt, &c->MU, &c->RA, &c->LA[0],
                    &c->LA[1], &c->LA[2], &c->seg, &c->curves64, &c->resid, &c->partial,
-                   &c->Jdev, &c->rho, &c->grad_a, &c->grad_b, &c->Wd, &c->Wn, &c->lohi};
+                   &c->Jdev, &c->rho, &c->grad_a, &c->grad_b, &c->Wd, &c->Wn, &c->lohi,
+                   &c->DxImg, &c->DyImg, &c->PImg};
   for (DevBuf* b : all) release(*b);
   for (cudaEvent_t e : c->events) cudaEventDestroy(e);
   delete c;
@@ -325,8 +342,11 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
   if (g->nx > 512 || g->ny > 512 || g->M > 64) return RTE_ERR_UNSUPPORTED;
   if (!(g->xmax > g->xmin) || !(g->ymax > g->ymin)) return RTE_ERR_INVALID_ARG;
   if (!(p->dt > 0) || !(o->c > 0) || !(o->n_in > 0) || !(o->n_out > 0) || std::fabs(o->g) >= 1.0 ||
-      p->ckpt_interval < 0 || p->precision != RTE_PREC_FP32)
+      p->ckpt_interval < 0 ||
+      (p->precision != RTE_PREC_FP32 && p->precision != RTE_PREC_TF32X3 && p->precision != RTE_PREC_TF32))
     return RTE_ERR_INVALID_ARG;
+  if (p->precision != RTE_PREC_FP32 && !rte_kern::tc_supported(g->nx, g->ny, g->M))
+    return RTE_ERR_UNSUPPORTED;
   rte_ctx* c = new (std::nothrow) rte_ctx();
   if (!c) return RTE_ERR_OOM;
   c->nx = g->nx; c->ny = g->ny; c->M = g->M;
@@ -336,6 +356,7 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
   c->opt = *o;
   c->par = *p;
   c->stream = static_cast<cudaStream_t>(stream);
+  c->tc_mode = p->precision;
   c->plane = static_cast<size_t>(g->nx) * g->ny * g->M;
   c->ring_len = 2 * g->nx + 2 * g->ny;
   auto fail = [&](rte_status s) { rte_destroy(c); return s; };
@@ -353,6 +374,15 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
       for (int k = 0; k < n; ++k) T[static_cast<size_t>(k) * n + i] = static_cast<float>(Dm[static_cast<size_t>(i) * n + k]);
     rte_status s = upload(*dst[ax], T, c->stream);
     if (s != RTE_OK) return fail(s);
+    if (c->tc_mode != 0) {
+      std::vector<float> img;
+      rte_setup::tc_operator_image(Dm, n, img);
+      s = upload(ax == 0 ? c->DxImg : c->DyImg, img, c->stream);
+      if (s != RTE_OK) return fail(s);
+      // the host vector must outlive the asynchronous copy
+      s = cuda_status(cudaStreamSynchronize(c->stream));
+      if (s != RTE_OK) return fail(s);
+    }
   }
   c->rho_dx = rte_setup::fc_spectral_radius(g->nx, c->dx, p->filter_alpha, p->filter_beta);
   c->rho_dy = rte_setup::fc_spectral_radius(g->ny, c->dy, p->filter_alpha, p->filter_beta);
@@ -380,6 +410,11 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
       area[static_cast<size_t>(j) * g->nx + i] = static_cast<float>(wx * wy);
     }
   rte_status s = RTE_OK;
+  std::vector<float> Pimg;
+  if (c->tc_mode != 0) {
+    rte_setup::tc_phase_image(P, g->M, Pimg);
+    s = upload(c->PImg, Pimg, c->stream);
+  }
   if (s == RTE_OK) s = upload(c->PT, PTf, c->stream);
   if (s == RTE_OK) s = upload(c->xi, xi, c->stream);
   if (s == RTE_OK) s = upload(c->eta, eta, c->stream);
@@ -458,7 +493,8 @@ rte_status rte_forward(rte_ctx* c, const rte_source_group* groups, int n_groups,
   rte_kern::BoundaryArgs b = boundary_args(c);
   b.S = F(c->S); b.A = F(c->A); b.T = F(c->T); b.kmax = kmax; b.T_len = n_steps;
   b.ring_out = F(c->ring); b.ring_steps = n_steps;
-  return march(c, c->U, c->R, c->L, c->hl, G, 0, n_steps, b, true, snap_index, fluence_out, nullptr);
+  RTE_TRY(march(c, c->U, c->R, c->L, c->hl, G, 0, n_steps, b, true, snap_index, fluence_out, nullptr));
+  return tc_check(c);
 }
 
 rte_status rte_detector_readout(rte_ctx* c, const rte_detector* dets, int n_det, float* curves_out) {
@@ -598,7 +634,8 @@ rte_status rte_adjoint_gradient(rte_ctx* c, const rte_detector* dets, int n_det,
   if (dJ_dmus)
     RTE_TRY(cuda_status(rte_kern::launch_to_float(D(c->grad_b), dJ_dmus, ncell, c->stream, &c->launches)));
   RTE_TRY(cuda_status(cudaMemcpyAsync(J_out, c->Jdev.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream)));
-  return cuda_status(cudaStreamSynchronize(c->stream));
+  RTE_TRY(cuda_status(cudaStreamSynchronize(c->stream)));
+  return tc_check(c);
 }
 
 }  // extern "C"

@@ -415,6 +415,7 @@ __global__ void to_float_kernel(const double* in, float* out, size_t n) {
 cudaError_t launch_step(const StepArgs& a, const BoundaryArgs& b, float* U, float* R,
                         const float* L1, const float* L2, float* L3, int step,
                         cudaStream_t s, long long* launches, cudaEvent_t* ev) {
+  if (a.tc_mode != 0) return launch_step_tc(a, b, U, R, L1, L2, L3, step, s, launches, ev);
   static bool attr_done = false;
   const size_t smx = pass_smem(a.nx, a.M, true), smy = pass_smem(a.ny, a.M, false);
   if (!attr_done) {

@@ -40,6 +40,12 @@ struct StepArgs {
   const float* mua;                 // [ny][nx]
   const float* mus;
   float cdt;                        // c * dt
+  // Tensor-core form: 0 = plain FP32 SIMT kernels, 1 = tcgen05 3xTF32,
+  // 2 = tcgen05 1xTF32; DxImg/DyImg hold the split, pre-swizzled operators.
+  int tc_mode;
+  const float* DxImg;
+  const float* DyImg;
+  const float* PImg;                // phase matrix as the scattering operand
 };
 
 // One AB4 step on all groups: x-pass (R = b P u - (a+b) u - xi d_x u), then
@@ -50,6 +56,15 @@ struct StepArgs {
 cudaError_t launch_step(const StepArgs& a, const BoundaryArgs& b, float* U, float* R,
                         const float* L1, const float* L2, float* L3, int step,
                         cudaStream_t s, long long* launches, cudaEvent_t* ev = nullptr);
+
+// tcgen05 form of launch_step (a.tc_mode != 0); see rte_tc.cu.
+bool tc_supported(int nx, int ny, int M);
+cudaError_t launch_step_tc(const StepArgs& a, const BoundaryArgs& b, float* U, float* R,
+                           const float* L1, const float* L2, float* L3, int step,
+                           cudaStream_t s, long long* launches, cudaEvent_t* ev);
+// Reads and clears the tcgen05 kernels' bounded-wait timeout flag
+// (synchronous).
+cudaError_t tc_take_error(int* flag);
 
 // Phi[g][j][i] = w sum_m u_m  (eq. photondensity).
 cudaError_t launch_fluence(const float* U, float* out, size_t out_group_stride, int nx, int ny,

@@ -3,7 +3,9 @@
 #include "rte_setup.h"
 
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
+#include <cstring>
 
 #include "fcgram_table.h"
 
@@ -64,6 +66,49 @@ void fc_derivative_matrix(int n, double h, double alpha, double beta,
       }
     }
   }
+}
+
+// Round an FP32 value to tf32 (10-bit mantissa), nearest with ties away
+// from zero: add half of the dropped range to the magnitude and truncate.
+static float tf32_round(float x) {
+  uint32_t b;
+  std::memcpy(&b, &x, 4);
+  if ((b & 0x7f800000u) == 0x7f800000u) return x;
+  b = (b + 0x1000u) & ~0x1fffu;
+  float r;
+  std::memcpy(&r, &b, 4);
+  return r;
+}
+
+void tc_operator_image(const std::vector<double>& D, int n, std::vector<float>& img) {
+  const int n_rows = (n + 127) / 128 * 128, n_kc = (n + 31) / 32;
+  img.assign(static_cast<size_t>(n_kc) * 2 * n_rows * 32, 0.f);
+  for (int q = 0; q < n_kc; ++q)
+    for (int i = 0; i < n; ++i)
+      for (int kk = 0; kk < 32; ++kk) {
+        const int k = q * 32 + kk;
+        if (k >= n) continue;
+        const double v = D[static_cast<size_t>(i) * n + k];
+        const float hi = tf32_round(static_cast<float>(v));
+        const float lo = tf32_round(static_cast<float>(v - static_cast<double>(hi)));
+        const size_t pos = static_cast<size_t>(i) * 32 + (((kk >> 2) ^ (i & 7)) << 2) + (kk & 3);
+        const size_t base = static_cast<size_t>(q) * 2 * n_rows * 32;
+        img[base + pos] = hi;
+        img[base + static_cast<size_t>(n_rows) * 32 + pos] = lo;
+      }
+}
+
+void tc_phase_image(const std::vector<double>& P, int M, std::vector<float>& img) {
+  img.assign(2 * 32 * 32, 0.f);
+  for (int m = 0; m < M; ++m)
+    for (int q = 0; q < M; ++q) {
+      const double v = P[static_cast<size_t>(m) * M + q];
+      const float hi = tf32_round(static_cast<float>(v));
+      const float lo = tf32_round(static_cast<float>(v - static_cast<double>(hi)));
+      const size_t pos = static_cast<size_t>(m) * 32 + (((q >> 2) ^ (m & 7)) << 2) + (q & 3);
+      img[pos] = hi;
+      img[32 * 32 + pos] = lo;
+    }
 }
 
 double fc_spectral_radius(int n, double h, double alpha, double beta) {

@@ -18,6 +18,17 @@ int smooth5(int n);
 void fc_derivative_matrix(int n, double h, double alpha, double beta,
                           std::vector<double>& D);
 
+// Split, pre-swizzled image of D for the tcgen05 kernels: for every chunk q
+// of 32 input positions, a hi tile then a lo tile, each n_rows (= n rounded
+// up to 128) rows x 32 tf32 values in the K-major 128-byte-swizzle order
+// (value (i, kk) at i*32 + ((kk/4) ^ (i%8))*4 + kk%4); hi = tf32(D),
+// lo = tf32(D - hi), zero padding outside n x n.
+void tc_operator_image(const std::vector<double>& D, int n, std::vector<float>& img);
+
+// Same split and swizzle for the phase matrix as the scattering operand:
+// rows m, K = q, 32 x 32 (zero-padded) hi tile then lo tile.
+void tc_phase_image(const std::vector<double>& P, int M, std::vector<float>& img);
+
 // Largest |multiplier| of the filtered periodic derivative on N_p points,
 // the spectral-radius estimate of D used by the stability check.
 double fc_spectral_radius(int n, double h, double alpha, double beta);
