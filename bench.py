@@ -37,18 +37,38 @@ WORKLOAD_DESC = ("tomo256_M32: 256x256 grid on [0,4]^2 cm, M=32 ordinates, backg
 # SIMT FP32 peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock).
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
+
+def load_peaks():
+    """Measured peaks (generated MEASURED_PEAKS.json), else the fallback
+    figures of one earlier GB300 measurement."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]), "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+PEAKS = load_peaks()
+
 # DRAM traffic per launch from an ncu capture, valid only for the kernel
 # source it was taken on (sha256 of csrc/rte_kernels.cu, first 16 hex digits).
 NCU_TRAFFIC = {
     # ncu --set full on the tomography workload's per-launch size (16 groups x
-    # 256^2 x 32): profiles/fcdom_passes_tomo256_ncu_full.md
+    # 256^2 x 32).  Plain FP32 SIMT passes (csrc/rte_kernels.cu):
+    # profiles/fcdom_passes_tomo256_ncu_full.md
     ("xpass_kernel", "7ec20f8a420c3adc"): 136.062464e6 + 86.956800e6,
     ("ypass_kernel", "7ec20f8a420c3adc"): 672.236800e6 + 234.185472e6,
+    # tcgen05 3xTF32 passes (csrc/rte_tc.cu): profiles/tc_passes_tomo256_ncu_full.md
+    ("tc_pass_kernel<x>", "995376ccd4b33508"): 136.286464e6 + 83.877888e6,
+    ("tc_pass_kernel<y>", "995376ccd4b33508"): 747.631872e6 + 236.092672e6,
 }
 
 
-def kernel_source_hash():
-    with open(os.path.join(ROOT, "paper_2202_09421_gb300", "csrc", "rte_kernels.cu"), "rb") as fh:
+def kernel_source_hash(name="tc_pass_kernel"):
+    src = "rte_tc.cu" if name.startswith("tc_pass") else "rte_kernels.cu"
+    with open(os.path.join(ROOT, "paper_2202_09421_gb300", "csrc", src), "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
@@ -200,23 +220,26 @@ def run_ours(args):
     updates = wl.updates
     a = torch.tensor(wl.mua, dtype=torch.float32, device=dev)
     b = torch.tensor(wl.mus, dtype=torch.float32, device=dev)
-    solver = FCDOMSolver(g, wl.optics, a, b, wl.c, wl.dt, ckpt_interval=0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
-    def one_step():
-        solver.forward(wl.groups, wl.n_steps, [wl.n_steps - 1])
-        return solver.readout(wl.detectors)
+    def time_form(precision, steps, warmup, clocks=None):
+        """Forward solve + detector readout per step; CUDA events on the
+        launching stream; L2 flushed before every timed step."""
+        solver = FCDOMSolver(g, wl.optics, a, b, wl.c, wl.dt, ckpt_interval=0, precision=precision)
 
-    for _ in range(args.warmup):
-        one_step()
-        flush.fill_(1.0)
-    barrier()
-    launches0 = solver.kernel_launches()
-    B.rte_set_kernel_timing(solver.ctx, True)
-    times = []
-    with ClockSampler(local) as clk:
-        for k in range(args.steps):
+        def one_step():
+            solver.forward(wl.groups, wl.n_steps, [wl.n_steps - 1])
+            return solver.readout(wl.detectors)
+
+        for _ in range(warmup):
+            one_step()
+            flush.fill_(1.0)
+        barrier()
+        launches0 = solver.kernel_launches()
+        B.rte_set_kernel_timing(solver.ctx, True)
+        times = []
+        for k in range(steps):
             flush.fill_(float(k))                  # evict the previous step from L2
             barrier()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -226,25 +249,48 @@ def run_ours(args):
             e1.record(stream)
             barrier()
             times.append(e0.elapsed_time(e1))
-    pass_ms, pass_cnt = B.rte_kernel_times(solver.ctx)
-    B.rte_set_kernel_timing(solver.ctx, False)
-    launches = solver.kernel_launches() - launches0
-    ms_step = max_over_ranks(statistics.mean(times))
+        pass_ms, pass_cnt = B.rte_kernel_times(solver.ctx)
+        B.rte_set_kernel_timing(solver.ctx, False)
+        launches = solver.kernel_launches() - launches0
+        return solver, max_over_ranks(statistics.mean(times)), pass_ms, pass_cnt, launches, one_step
+
+    # Headline: tcgen05 tensor-core form with split 3xTF32 operands (FP32-level
+    # accuracy; the forward parity tests hold it to 1e-5 against FP64).
+    with ClockSampler(local) as clk:
+        solver, ms_step, pass_ms, pass_cnt, launches, one_step = time_form(
+            B.RTE_PREC_TF32X3, args.steps, args.warmup)
     value = updates * world / (ms_step / 1e3)
 
-    # Roofline of the dominant pass (dense FC-operator products on FP32 SIMT).
+    # Roofline of the dominant pass.  y-pass: algorithmic 28 B per update
+    # (read u, R, L1..L3; write u, L) against HBM; x-pass: tensor-core flops
+    # (3 products x 2 flop x (n + M) per update) against the TF32 peak.
     ncell_m = g.nx * g.ny * g.M * len(wl.groups)
-    flops = [ncell_m * (2 * g.nx + 2 * g.M + 5), ncell_m * (2 * g.ny + 12)]
-    names = ["xpass_kernel", "ypass_kernel"]
+    names = ["tc_pass_kernel<x>", "tc_pass_kernel<y>"]
     dom = 0 if pass_ms[0] >= pass_ms[1] else 1
     avg_ms = pass_ms[dom] / max(1, pass_cnt[dom])
-    achieved = flops[dom] / (avg_ms / 1e3) / 1e12
-    traffic = NCU_TRAFFIC.get((names[dom], kernel_source_hash()))
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": names[dom], "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                "pass_ms_per_launch": [pass_ms[0] / max(1, pass_cnt[0]), pass_ms[1] / max(1, pass_cnt[1])],
-                "pass_share": [pass_ms[0] / sum(pass_ms), pass_ms[1] / sum(pass_ms)]}
+    if dom == 1:
+        achieved = 28.0 * ncell_m / (avg_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": PEAKS["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / PEAKS["hbm_gbs"], "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        flops = 3 * 2 * (g.nx + g.M) * ncell_m
+        peak = PEAKS["bf16_tflops"] / 2.0
+        achieved = flops / (avg_ms / 1e3) / 1e12
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "peak_source": "measured bf16 burst x 1/2 (tf32 nominal ratio)"}
+    roofline.update({"traffic": NCU_TRAFFIC.get((names[dom], kernel_source_hash(names[dom]))),
+                     "kernel": names[dom],
+                     "pass_ms_per_launch": [pass_ms[0] / max(1, pass_cnt[0]), pass_ms[1] / max(1, pass_cnt[1])],
+                     "pass_share": [pass_ms[0] / sum(pass_ms), pass_ms[1] / sum(pass_ms)]})
+
+    # The other forms on the same workload: the plain FP32 SIMT form (the
+    # metric's comparison) and the single-product TF32 reduced-precision form.
+    forms = {}
+    for name, prec in (("plain_fp32_simt", B.RTE_PREC_FP32), ("tf32_reduced", B.RTE_PREC_TF32)):
+        s2, ms2, _, _, _, _ = time_form(prec, 1, 1)
+        s2.close()
+        forms[name] = {"value": updates * world / (ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2,
+                       "headline_speedup": ms2 / ms_step}
 
     # End to end through the public API with host buffers: copy the medium
     # from pinned host memory, solve, read the detector curves back.
@@ -275,11 +321,12 @@ def run_ours(args):
         am = torch.tensor(wm.mua, dtype=torch.float32, device=dev)
         bm = torch.tensor(wm.mus, dtype=torch.float32, device=dev)
         st = FCDOMSolver(tgt.grid, tgt.optics, torch.tensor(tgt.mua, dtype=torch.float32, device=dev),
-                         bm, tgt.c, tgt.dt, ckpt_interval=0)
+                         bm, tgt.c, tgt.dt, ckpt_interval=0, precision=B.RTE_PREC_TF32X3)
         st.forward(tgt.groups, tgt.n_steps)
         measured = st.readout(tgt.detectors)
         st.close()
-        sa = FCDOMSolver(wm.grid, wm.optics, am, bm, wm.c, wm.dt, ckpt_interval=100)
+        sa = FCDOMSolver(wm.grid, wm.optics, am, bm, wm.c, wm.dt, ckpt_interval=100,
+                         precision=B.RTE_PREC_TF32X3)
         gt = []
         for k in range(2):
             flush.fill_(float(k))
@@ -309,11 +356,12 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC, "form": "plain FP32 SIMT (dense FC operators)",
+            "config": {"workload": WORKLOAD_DESC,
+                       "form": "tcgen05 tensor cores, split 3xTF32 operands (FP32-level accuracy)",
                        "updates_per_step": updates * world, "l2": "flushed between timed steps "
                        "(256 MB write) and state > L2", "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks, "adjoint": adjoint,
+            "clocks": clocks, "adjoint": adjoint, "forms": forms,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

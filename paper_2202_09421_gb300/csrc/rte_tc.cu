@@ -35,6 +35,7 @@
 // and commits them to mbarriers; every wait is bounded and sets g_tc_error
 // instead of spinning forever.
 #include <cstdint>
+#include <cstdlib>
 
 #include "rte_kernels.cuh"
 
@@ -148,8 +149,8 @@ struct TcLayout {
 
 constexpr int kPBytes = 2 * 32 * 128;   // P~ operand image: hi and lo, 32 rows x 128 B
 
-template <bool XPASS, bool X3>
-__global__ void __launch_bounds__(kThreads, 1)
+template <bool XPASS, bool X3, int NSTAGE>
+__global__ void __launch_bounds__(kThreads, NSTAGE == 1 ? 2 : 1)
     tc_pass_kernel(StepArgs a, BoundaryArgs b, float* __restrict__ U, float* __restrict__ R,
                    const float* __restrict__ L1, const float* __restrict__ L2, float* __restrict__ L3,
                    int src_step, int ring_step) {
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int n_lines = XPASS ? ny : nx;        // rows (x) / columns (y) of the grid
 
   unsigned char* sm = smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023);
-  unsigned char* Psm = sm + 2 * L.stage_bytes;     // P~ image (x-pass)
+  unsigned char* Psm = sm + NSTAGE * L.stage_bytes;     // P~ image (x-pass)
   const uint32_t bar_full0 = smem_u32(&bars[0]), bar_done0 = smem_u32(&bars[2]);
   const uint32_t bar_p = smem_u32(&bars[4]), bar_scat = smem_u32(&bars[5]);
 
@@ -226,13 +227,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   };
   load_chunk(0);
   for (int q = 0; q < L.n_kc; ++q) {
-    const int s = q & 1;
+    const int s = q % NSTAGE;
     unsigned char* stage = sm + s * L.stage_bytes;
     unsigned char* Dhi = stage;                                   // n_mt tiles
     unsigned char* Dlo = stage + L.n_mt * kTileBytes;             // (3xTF32)
     unsigned char* Shi = stage + (X3 ? 2 : 1) * L.n_mt * kTileBytes;
     unsigned char* Slo = Shi + kTileBytes;
-    if (q >= 2) ok = mbar_wait(bar_done0 + 8 * s, ((q - 2) >> 1) & 1) && ok;
+    if (q >= NSTAGE) ok = mbar_wait(bar_done0 + 8 * s, ((q - NSTAGE) / NSTAGE) & 1) && ok;
     if (tid == 0) {
       // image chunk: [hi: nrows_img x 32][lo: nrows_img x 32] -> Dhi, Dlo contiguous
       bulk_copy(smem_u32(Dhi), Dimg + q * chunk_floats, (X3 ? 2 : 1) * nrows_img * 128, bar_full0 + 8 * s);
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     if (q + 1 < L.n_kc) load_chunk(q + 1);
     if (tid == 0) {
-      ok = mbar_wait(bar_full0 + 8 * s, (q >> 1) & 1) && ok;
+      ok = mbar_wait(bar_full0 + 8 * s, (q / NSTAGE) & 1) && ok;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint64_t dSh = sw128_desc(smem_u32(Shi)), dSl = sw128_desc(smem_u32(Slo));
       if (XPASS) {
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mma_commit(bar_done0 + 8 * s);
     }
   }
-  ok = mbar_wait(bar_done0 + 8 * ((L.n_kc - 1) & 1), ((L.n_kc - 1) >> 1) & 1) && ok;
+  ok = mbar_wait(bar_done0 + 8 * ((L.n_kc - 1) % NSTAGE), ((L.n_kc - 1) / NSTAGE) & 1) && ok;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   // ---------------- x-pass: scattering contraction into the same tiles ----------------
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                              (static_cast<uint32_t>((M < 16 ? 16 : M) >> 3) << 17) |
                              (static_cast<uint32_t>(kMT >> 4) << 24);
     const int slot_bytes = (X3 ? 2 : 1) * kTileBytes;
-    const int slots = (2 * L.stage_bytes) / slot_bytes;
+    const int slots = (NSTAGE * L.stage_bytes) / slot_bytes;
     const int pairs = L.n_mt * per_tile;
     if (tid == 0) ok = mbar_wait(bar_p, 0) && ok;
     const uint64_t dPh = sw128_desc(smem_u32(Psm)), dPl = sw128_desc(smem_u32(Psm + 32 * 128));
@@ -509,21 +510,41 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L.tmem_cols));
 }
 
-template <bool XPASS, bool X3>
+template <bool XPASS, bool X3, int NSTAGE>
 cudaError_t launch_one(const StepArgs& a, const BoundaryArgs& b, float* U, float* R, const float* L1,
                        const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s) {
   const TcLayout L(XPASS ? a.nx : a.ny, X3);
-  const size_t smem = 1024 + 2 * static_cast<size_t>(L.stage_bytes) + kPBytes;
+  const size_t smem = 1024 + NSTAGE * static_cast<size_t>(L.stage_bytes) + kPBytes;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(tc_pass_kernel<XPASS, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448 - 2048);
+    cudaFuncSetAttribute(tc_pass_kernel<XPASS, X3, NSTAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         232448 - 2048);
     attr = true;
   }
   const int per_tile = kNC / a.M;
   const int lines = XPASS ? a.ny : a.nx;
   dim3 grid((lines + per_tile - 1) / per_tile, 1, a.G);
-  tc_pass_kernel<XPASS, X3><<<grid, kThreads, smem, s>>>(a, b, U, R, L1, L2, L3, src_step, ring_step);
+  tc_pass_kernel<XPASS, X3, NSTAGE><<<grid, kThreads, smem, s>>>(a, b, U, R, L1, L2, L3, src_step, ring_step);
   return cudaGetLastError();
+}
+
+// One stage and two CTAs per SM (one CTA's epilogue overlaps the other's
+// tensor-core main loop) when RTE_TC_STAGES is unset or 1; two stages and one
+// CTA per SM when it is 2.
+int tc_stages() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("RTE_TC_STAGES");
+    v = (e && e[0] == '2') ? 2 : 1;
+  }
+  return v;
+}
+
+template <bool XPASS, bool X3>
+cudaError_t launch_pass(const StepArgs& a, const BoundaryArgs& b, float* U, float* R, const float* L1,
+                        const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s) {
+  if (tc_stages() == 2) return launch_one<XPASS, X3, 2>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
+  return launch_one<XPASS, X3, 1>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
 }
 
 }  // namespace
@@ -538,12 +559,12 @@ cudaError_t launch_step_tc(const StepArgs& a, const BoundaryArgs& b, float* U, f
   const int ring_step = b.ring_out ? step : -1;
   cudaError_t e;
   if (ev) cudaEventRecord(ev[0], s);
-  e = a.tc_mode == 2 ? launch_one<true, false>(a, b, U, R, L1, L2, L3, step, ring_step, s)
-                     : launch_one<true, true>(a, b, U, R, L1, L2, L3, step, ring_step, s);
+  e = a.tc_mode == 2 ? launch_pass<true, false>(a, b, U, R, L1, L2, L3, step, ring_step, s)
+                     : launch_pass<true, true>(a, b, U, R, L1, L2, L3, step, ring_step, s);
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[1], s);
-  e = a.tc_mode == 2 ? launch_one<false, false>(a, b, U, R, L1, L2, L3, step, ring_step, s)
-                     : launch_one<false, true>(a, b, U, R, L1, L2, L3, step, ring_step, s);
+  e = a.tc_mode == 2 ? launch_pass<false, false>(a, b, U, R, L1, L2, L3, step, ring_step, s)
+                     : launch_pass<false, true>(a, b, U, R, L1, L2, L3, step, ring_step, s);
   if (ev) cudaEventRecord(ev[2], s);
   if (launches) *launches += 2;
   return e;
