@@ -148,6 +148,8 @@ struct TcLayout {
 };
 
 constexpr int kPBytes = 2 * 32 * 128;   // P~ operand image: hi and lo, 32 rows x 128 B
+// y-pass epilogue: two 5-array buffers, three [16][128] tiles, boundary tables
+constexpr size_t kEpiBytes = (2 * 5 * 16 + 3 * 16) * 128 * 4 + (8 + 4 + 8) * 32 * 4 + 8 * 32;
 
 template <bool XPASS, bool X3, int NSTAGE>
 __global__ void __launch_bounds__(kThreads, NSTAGE == 1 ? 2 : 1)
@@ -380,21 +382,62 @@ __global__ void __launch_bounds__(kThreads, NSTAGE == 1 ? 2 : 1)
       }
     }
   } else {
-    // acc[lane = slab column c][column = output row j].  Per chunk of 16 rows:
-    // warps 0-3 copy the accumulator to a shared [16][128] tile, then all
-    // threads stream the chunk's rows with float4 accesses (each grid row of
-    // the slab is 128 contiguous floats), and boundary nodes are finished
-    // from the pre-BC values kept in shared memory.
-    float* acc_s = reinterpret_cast<float*>(sm);                 // [16][128]
+    // acc[lane = slab column c][column = output row j].  Per chunk of 16 grid
+    // rows: every thread copies its own float4 items of u, R, L1, L2, L3 into
+    // a shared double buffer with cp.async one chunk ahead (so a chunk's loads
+    // overlap the previous chunk's work, and each thread reads back only what
+    // it copied); warps 0-3 copy the accumulator to a shared [16][128] tile;
+    // all threads form AB4 with float4 accesses; boundary nodes are finished
+    // from the pre-BC values kept in shared memory.  Uses the stage and P~
+    // regions (104 KB), free after the main loop.
+    constexpr int kEpiArr = 5;                                   // u, R, L1, L2, L3
+    constexpr int kBufFloats = kEpiArr * 16 * kNC;               // 40 KB
+    float* ebuf = reinterpret_cast<float*>(sm);                  // [2][5][16][128]
+    float* acc_s = ebuf + 2 * kBufFloats;                        // [16][128]
     float* un_s = acc_s + 16 * kNC;                              // [16][128] pre-BC u^{k+1}
     float* bc_s = un_s + 16 * kNC;                               // [16][128] post-BC values
     const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * quarter) << 16);
     const bool tile_has_xface = (t0 == 0) || (t0 + per_tile > nx - 1);
     const int ring_len = 2 * ny + 2 * nx;
     const int wcols = min(per_tile, nx - t0);                    // valid grid columns of the tile
-    for (int ci = 0; ci < nrows_img / 16; ++ci) {
+    const int nchunks = min(nrows_img / 16, (ny + 15) / 16);
+    const float* srcs[kEpiArr] = {U, R, L1, L2, L3};
+    // Boundary tables (faces 0..3, corners 4..7) staged once per CTA.
+    float* bc_f = bc_s + 16 * kNC;                               // [8][M]
+    float* bc_wexit = bc_f + 8 * 32;                             // [4][M]
+    int* bc_refl = reinterpret_cast<int*>(bc_wexit + 4 * 32);    // [8][M]
+    unsigned char* bc_act = reinterpret_cast<unsigned char*>(bc_refl + 8 * 32);   // [8][M]
+    for (int e = tid; e < 8 * M; e += kThreads) {
+      const int tb = e / M, m = e - tb * M;
+      const bool face = tb < 4;
+      const int k = (face ? tb : tb - 4) * M + m;
+      bc_f[e] = face ? b.face_f[k] : b.corner_f[k];
+      bc_refl[e] = face ? b.face_refl[k] : b.corner_refl[k];
+      bc_act[e] = face ? b.face_act[k] : b.corner_act[k];
+      if (face) bc_wexit[e] = b.wexit[k];
+    }
+    auto issue_chunk = [&](int cc, int bsel) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int item = tid + h * kThreads;                   // 16 rows x 32 float4
+        const int t = item >> 5, c = (item & 31) * 4;
+        const int j = cc * 16 + t;
+        if (c / M >= wcols || j >= ny) continue;
+        const size_t gidx = goff + (static_cast<size_t>(j) * nx + t0) * M + c;
+#pragma unroll
+        for (int arr = 0; arr < kEpiArr; ++arr) {
+          float* dst = ebuf + bsel * kBufFloats + (arr * 16 + t) * kNC + c;
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(srcs[arr] + gidx)
+                       : "memory");
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (ok) issue_chunk(0, 0);
+    for (int ci = 0; ci < nchunks; ++ci) {
       const int j0c = ci * 16;
-      if (j0c >= ny) break;                                      // uniform across the CTA
+      const int bsel = ci & 1;
+      if (ok && ci + 1 < nchunks) issue_chunk(ci + 1, bsel ^ 1);
       if (warp < 4) {
         float acc[16];
         tmem_ld16(tbase + j0c, acc);
@@ -402,89 +445,94 @@ __global__ void __launch_bounds__(kThreads, NSTAGE == 1 ? 2 : 1)
 #pragma unroll
         for (int t = 0; t < 16; ++t) acc_s[t * kNC + c] = acc[t];
       }
+      if (ci + 1 < nchunks)
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+      else
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
       __syncthreads();
       // CTA-uniform (barriers below depend on it).
       const bool chunk_bnd = j0c == 0 || j0c + 16 > ny - 1 || tile_has_xface;
-      if (ok) {
-        float4 u4[2], r4[2], p4[2], q4[2], s4[2];
-        size_t base[2];
-        bool valid[2];
+      const float* buf = ebuf + bsel * kBufFloats;
+      const bool got = ok;
+      if (got) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int item = tid + h * kThreads;               // 16 rows x 32 float4
+          const int item = tid + h * kThreads;               // this thread's own copies
           const int t = item >> 5, c = (item & 31) * 4;
-          const int w = c / M, m0 = c - w * M;
-          const int j = j0c + t;
-          valid[h] = w < wcols && j < ny;
-          base[h] = goff + (static_cast<size_t>(j) * nx + (t0 + w)) * M + m0;
-          if (valid[h]) {
-            u4[h] = *reinterpret_cast<const float4*>(U + base[h]);
-            r4[h] = *reinterpret_cast<const float4*>(R + base[h]);
-            p4[h] = *reinterpret_cast<const float4*>(L1 + base[h]);
-            q4[h] = *reinterpret_cast<const float4*>(L2 + base[h]);
-            s4[h] = *reinterpret_cast<const float4*>(L3 + base[h]);
-          }
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (!valid[h]) continue;
-          const int item = tid + h * kThreads;
-          const int t = item >> 5, c = (item & 31) * 4;
+          const int w = c / M, j = j0c + t, i = t0 + w;
+          if (w >= wcols || j >= ny) continue;
+          const float4 u4 = *reinterpret_cast<const float4*>(buf + (0 * 16 + t) * kNC + c);
+          const float4 r4 = *reinterpret_cast<const float4*>(buf + (1 * 16 + t) * kNC + c);
+          const float4 p4 = *reinterpret_cast<const float4*>(buf + (2 * 16 + t) * kNC + c);
+          const float4 q4 = *reinterpret_cast<const float4*>(buf + (3 * 16 + t) * kNC + c);
+          const float4 s4 = *reinterpret_cast<const float4*>(buf + (4 * 16 + t) * kNC + c);
           const float4 ac = *reinterpret_cast<const float4*>(acc_s + t * kNC + c);
           float4 lk, un;
-          lk.x = r4[h].x + ac.x; lk.y = r4[h].y + ac.y; lk.z = r4[h].z + ac.z; lk.w = r4[h].w + ac.w;
-          un.x = fmaf(a.cdt, kAB0 * lk.x + kAB1 * p4[h].x + kAB2 * q4[h].x + kAB3 * s4[h].x, u4[h].x);
-          un.y = fmaf(a.cdt, kAB0 * lk.y + kAB1 * p4[h].y + kAB2 * q4[h].y + kAB3 * s4[h].y, u4[h].y);
-          un.z = fmaf(a.cdt, kAB0 * lk.z + kAB1 * p4[h].z + kAB2 * q4[h].z + kAB3 * s4[h].z, u4[h].z);
-          un.w = fmaf(a.cdt, kAB0 * lk.w + kAB1 * p4[h].w + kAB2 * q4[h].w + kAB3 * s4[h].w, u4[h].w);
-          *reinterpret_cast<float4*>(L3 + base[h]) = lk;
-          const int w = c / M, j = j0c + t, i = t0 + w;
+          lk.x = r4.x + ac.x; lk.y = r4.y + ac.y; lk.z = r4.z + ac.z; lk.w = r4.w + ac.w;
+          un.x = fmaf(a.cdt, kAB0 * lk.x + kAB1 * p4.x + kAB2 * q4.x + kAB3 * s4.x, u4.x);
+          un.y = fmaf(a.cdt, kAB0 * lk.y + kAB1 * p4.y + kAB2 * q4.y + kAB3 * s4.y, u4.y);
+          un.z = fmaf(a.cdt, kAB0 * lk.z + kAB1 * p4.z + kAB2 * q4.z + kAB3 * s4.z, u4.z);
+          un.w = fmaf(a.cdt, kAB0 * lk.w + kAB1 * p4.w + kAB2 * q4.w + kAB3 * s4.w, u4.w);
+          const size_t gidx = goff + (static_cast<size_t>(j) * nx + t0) * M + c;
+          *reinterpret_cast<float4*>(L3 + gidx) = lk;
           const bool bnd = i == 0 || i == nx - 1 || j == 0 || j == ny - 1;
           if (chunk_bnd) *reinterpret_cast<float4*>(un_s + t * kNC + c) = un;
-          if (!bnd) *reinterpret_cast<float4*>(U + base[h]) = un;
+          if (!bnd) *reinterpret_cast<float4*>(U + gidx) = un;
         }
       }
       if (chunk_bnd) {
         // eq. (RTE) third line on the chunk's boundary nodes, from the pre-BC
-        // values of the node (un_s); results in bc_s and in U.
+        // values of the node (un_s); results in bc_s and in U.  Boundary
+        // nodes of the chunk: the x-face column (tiles at i = 0 / nx-1) on
+        // every row, and the y-face rows j = 0 / ny-1 on every column.
         __syncthreads();
-        for (int e = tid; e < 16 * wcols * M; e += kThreads) {
-          const int t = e / (wcols * M), c = e - t * (wcols * M);
-          const int w = c / M, m = c - w * M;
-          const int j = j0c + t, i = t0 + w;
-          if (j >= ny) continue;
-          const bool lf = i == 0, rt = i == nx - 1, bt = j == 0, tp = j == ny - 1;
-          if (!(lf || rt || bt || tp)) continue;
-          const int* refl;
-          const float* fco;
-          const unsigned char* act;
-          if ((lf || rt) && (bt || tp)) {
-            const int cix = (rt ? 1 : 0) + (tp ? 2 : 0);
-            refl = b.corner_refl + cix * M; fco = b.corner_f + cix * M; act = b.corner_act + cix * M;
+        const int xcol = (t0 == 0) ? 0 : (t0 + wcols - 1 == nx - 1 ? wcols - 1 : -1);
+        const int yrow0 = (j0c == 0) ? 0 : -1;
+        const int yrow1 = (ny - 1 >= j0c && ny - 1 < j0c + 16) ? ny - 1 - j0c : -1;
+        const int rows = min(16, ny - j0c);
+        // cells: [x-face column on each row][y-face rows on each column]
+        const int n_xcells = xcol >= 0 ? rows : 0;
+        const int n_ycells = ((yrow0 >= 0) + (yrow1 >= 0 && yrow1 != yrow0)) * wcols;
+        for (int e = tid; e < (n_xcells + n_ycells) * M; e += kThreads) {
+          const int cidx = e / M, m = e - cidx * M;
+          int t, w;
+          if (cidx < n_xcells) {
+            t = cidx;
+            w = xcol;
           } else {
-            const int F = lf ? 0 : rt ? 1 : bt ? 2 : 3;
-            refl = b.face_refl + F * M; fco = b.face_f + F * M; act = b.face_act + F * M;
+            const int yc = cidx - n_xcells;
+            t = (yc / wcols == 0 && yrow0 >= 0) ? yrow0 : yrow1;
+            w = yc % wcols;
+            if (xcol >= 0 && w == xcol) continue;                // corner: done as x-face cell
           }
+          const int j = j0c + t, i = t0 + w;
+          if (!got) continue;
+          const bool lf = i == 0, rt = i == nx - 1, bt = j == 0, tp = j == ny - 1;
+          int tb;                                                // table: face 0..3 or corner 4..7
+          if ((lf || rt) && (bt || tp)) tb = 4 + (rt ? 1 : 0) + (tp ? 2 : 0);
+          else tb = lf ? 0 : rt ? 1 : bt ? 2 : 3;
           const float* pre = un_s + t * kNC + w * M;
           float val = pre[m];
-          if (act[m]) {
+          if (bc_act[tb * M + m]) {
             const int node = lf ? j : rt ? ny + j : bt ? 2 * ny + i : 2 * ny + nx + i;
             float qv = 0.f;
             for (int k = 0; k < b.kmax; ++k) {
               const size_t gk = static_cast<size_t>(g) * b.kmax + k;
-              qv = fmaf(b.S[gk * ring_len + node] * b.A[gk * M + m], b.T[gk * b.T_len + src_step], qv);
+              qv = fmaf(__ldg(b.S + gk * ring_len + node) * __ldg(b.A + gk * M + m),
+                        __ldg(b.T + gk * b.T_len + src_step), qv);
             }
+            const float fco = bc_f[tb * M + m];
             if (b.rho)
-              qv = fmaf(1.0f - fco[m], b.rho[(static_cast<size_t>(g) * b.rho_len + src_step) * ring_len + node], qv);
-            val = fmaf(fco[m], pre[refl[m]], qv);
+              qv = fmaf(1.0f - fco, __ldg(b.rho + (static_cast<size_t>(g) * b.rho_len + src_step) * ring_len + node), qv);
+            val = fmaf(fco, pre[bc_refl[tb * M + m]], qv);
           }
-          bc_s[t * kNC + c] = val;
+          bc_s[t * kNC + w * M + m] = val;
           U[goff + (static_cast<size_t>(j) * nx + i) * M + m] = val;
         }
         __syncthreads();
         // Exitance of eq. (OpMed): one thread per (boundary node, face), in a
         // fixed summation order.
-        if (b.ring_out && ring_step >= 0) {
+        if (got && b.ring_out && ring_step >= 0) {
           float* ro = b.ring_out + (static_cast<size_t>(g) * b.ring_steps + ring_step) * ring_len;
           for (int e = tid; e < 16 * wcols * 2; e += kThreads) {
             const int t = e / (wcols * 2), rem = e - t * (wcols * 2), w = rem >> 1, fy = rem & 1;
@@ -496,7 +544,7 @@ __global__ void __launch_bounds__(kThreads, NSTAGE == 1 ? 2 : 1)
             const int F = fy == 0 ? (lf ? 0 : 1) : (bt ? 2 : 3);
             const float* val = bc_s + t * kNC + w * M;
             float ex = 0.f;
-            for (int m = 0; m < M; ++m) ex = fmaf(b.wexit[F * M + m], val[m], ex);
+            for (int m = 0; m < M; ++m) ex = fmaf(bc_wexit[F * M + m], val[m], ex);
             ro[fy == 0 ? (lf ? j : ny + j) : (bt ? 2 * ny + i : 2 * ny + nx + i)] = ex;
           }
         }
@@ -514,7 +562,9 @@ template <bool XPASS, bool X3, int NSTAGE>
 cudaError_t launch_one(const StepArgs& a, const BoundaryArgs& b, float* U, float* R, const float* L1,
                        const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s) {
   const TcLayout L(XPASS ? a.nx : a.ny, X3);
-  const size_t smem = 1024 + NSTAGE * static_cast<size_t>(L.stage_bytes) + kPBytes;
+  // The y-pass epilogue reuses the stage and P~ regions for 104 KB of buffers.
+  const size_t body = NSTAGE * static_cast<size_t>(L.stage_bytes) + kPBytes;
+  const size_t smem = 1024 + (XPASS ? body : (body > kEpiBytes ? body : kEpiBytes));
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(tc_pass_kernel<XPASS, X3, NSTAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
