@@ -61,8 +61,8 @@ NCU_TRAFFIC = {
     ("xpass_kernel", "7ec20f8a420c3adc"): 136.062464e6 + 86.956800e6,
     ("ypass_kernel", "7ec20f8a420c3adc"): 672.236800e6 + 234.185472e6,
     # tcgen05 3xTF32 passes (csrc/rte_tc.cu): profiles/tc_passes_tomo256_ncu_full.md
-    ("tc_pass_kernel<x>", "995376ccd4b33508"): 136.286464e6 + 83.877888e6,
-    ("tc_pass_kernel<y>", "995376ccd4b33508"): 747.631872e6 + 236.092672e6,
+    ("tc_pass_kernel<x>", "a1462982e931f755"): 136.674304e6 + 84.280320e6,
+    ("tc_pass_kernel<y>", "a1462982e931f755"): 751.340032e6 + 234.558208e6,
 }
 
 

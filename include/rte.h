@@ -78,11 +78,19 @@ typedef struct rte_optics {
 #define RTE_PREC_FP32 0
 #define RTE_PREC_TF32X3 1
 #define RTE_PREC_TF32 2
+/* flags: RTE_FLAG_TC_SCATTER computes the x-pass scattering sum as a tcgen05
+ * contraction into the operator accumulator (same operand split as the
+ * precision); without it the tensor-core forms evaluate the circulant
+ * scattering sum in FP32 on the CUDA cores of the x-pass epilogue, which
+ * measured faster on GB300 (0.158 vs 0.190 ms per x-pass at 256^2, M = 32,
+ * 16 groups). */
+#define RTE_FLAG_TC_SCATTER 1
 typedef struct rte_params {
   double dt;
   double filter_alpha, filter_beta;
   int ckpt_interval;
   int precision;
+  int flags;
 } rte_params;
 
 /* One laser beam s_k of eq. (RTEsources2): position (x, y) on the boundary,

@@ -17,6 +17,7 @@ from .build import LIB
 RTE_PREC_FP32 = 0      # plain FP32 SIMT kernels
 RTE_PREC_TF32X3 = 1    # tcgen05, split 3xTF32 operands (FP32-level accuracy)
 RTE_PREC_TF32 = 2      # tcgen05, one TF32 product (reduced precision)
+RTE_FLAG_TC_SCATTER = 1  # x-pass scattering as a tcgen05 contraction
 
 
 class RteGrid(ctypes.Structure):
@@ -31,7 +32,7 @@ class RteOptics(ctypes.Structure):
 
 class RteParams(ctypes.Structure):
     _fields_ = [("dt", c_double), ("filter_alpha", c_double), ("filter_beta", c_double),
-                ("ckpt_interval", c_int), ("precision", c_int)]
+                ("ckpt_interval", c_int), ("precision", c_int), ("flags", c_int)]
 
 
 class RteBeam(ctypes.Structure):

@@ -131,6 +131,7 @@ rte_kern::StepArgs step_args(rte_ctx* c, int G) {
   a.xi = F(c->xi); a.eta = F(c->eta); a.mua = F(c->mua); a.mus = F(c->mus);
   a.cdt = static_cast<float>(c->opt.c * c->par.dt);
   a.tc_mode = c->tc_mode;
+  a.tc_scatter = (c->par.flags & RTE_FLAG_TC_SCATTER) ? 1 : 0;
   a.DxImg = F(c->DxImg);
   a.DyImg = F(c->DyImg);
   a.PImg = F(c->PImg);
@@ -342,7 +343,7 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
   if (g->nx > 512 || g->ny > 512 || g->M > 64) return RTE_ERR_UNSUPPORTED;
   if (!(g->xmax > g->xmin) || !(g->ymax > g->ymin)) return RTE_ERR_INVALID_ARG;
   if (!(p->dt > 0) || !(o->c > 0) || !(o->n_in > 0) || !(o->n_out > 0) || std::fabs(o->g) >= 1.0 ||
-      p->ckpt_interval < 0 ||
+      p->ckpt_interval < 0 || (p->flags & ~RTE_FLAG_TC_SCATTER) != 0 ||
       (p->precision != RTE_PREC_FP32 && p->precision != RTE_PREC_TF32X3 && p->precision != RTE_PREC_TF32))
     return RTE_ERR_INVALID_ARG;
   if (p->precision != RTE_PREC_FP32 && !rte_kern::tc_supported(g->nx, g->ny, g->M))

@@ -43,6 +43,7 @@ struct StepArgs {
   // Tensor-core form: 0 = plain FP32 SIMT kernels, 1 = tcgen05 3xTF32,
   // 2 = tcgen05 1xTF32; DxImg/DyImg hold the split, pre-swizzled operators.
   int tc_mode;
+  int tc_scatter;                   // x-pass scattering as a tcgen05 contraction
   const float* DxImg;
   const float* DyImg;
   const float* PImg;                // phase matrix as the scattering operand

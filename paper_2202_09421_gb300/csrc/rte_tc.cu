@@ -35,7 +35,6 @@
 // and commits them to mbarriers; every wait is bounded and sets g_tc_error
 // instead of spinning forever.
 #include <cstdint>
-#include <cstdlib>
 
 #include "rte_kernels.cuh"
 
@@ -151,7 +150,7 @@ constexpr int kPBytes = 2 * 32 * 128;   // P~ operand image: hi and lo, 32 rows 
 // y-pass epilogue: two 5-array buffers, three [16][128] tiles, boundary tables
 constexpr size_t kEpiBytes = (2 * 5 * 16 + 3 * 16) * 128 * 4 + (8 + 4 + 8) * 32 * 4 + 8 * 32;
 
-template <bool XPASS, bool X3, int NSTAGE>
+template <bool XPASS, bool X3, int NSTAGE, int MM, bool SCAT_TC>
 __global__ void __launch_bounds__(kThreads, NSTAGE == 1 ? 2 : 1)
     tc_pass_kernel(StepArgs a, BoundaryArgs b, float* __restrict__ U, float* __restrict__ R,
                    const float* __restrict__ L1, const float* __restrict__ L2, float* __restrict__ L3,
@@ -159,7 +158,8 @@ __global__ void __launch_bounds__(kThreads, NSTAGE == 1 ? 2 : 1)
   extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bars[6];   // full[2], done[2], p_full, scat_done
   __shared__ uint32_t tmem_slot;
-  const int nx = a.nx, ny = a.ny, M = a.M;
+  const int nx = a.nx, ny = a.ny;
+  constexpr int M = MM;
   const int n = XPASS ? nx : ny;
   const TcLayout L(n, X3);
   const int per_tile = kNC / M;               // grid rows (x) or columns (y) per tile
@@ -291,35 +291,49 @@ __global__ void __launch_bounds__(kThreads, NSTAGE == 1 ? 2 : 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   // ---------------- x-pass: scattering contraction into the same tiles ----------------
-  if (XPASS) {
+  if (XPASS && SCAT_TC) {
     // (t, r) pairs: 128 output positions of tile t on grid row j0 + r.  A =
     // b(r, i) u(r, i, q) (K = q padded to 32), B = P~ rows m; N = max(M, 16).
     const uint32_t idesc_s = (1u << 4) | (2u << 7) | (2u << 10) |
                              (static_cast<uint32_t>((M < 16 ? 16 : M) >> 3) << 17) |
                              (static_cast<uint32_t>(kMT >> 4) << 24);
     const int slot_bytes = (X3 ? 2 : 1) * kTileBytes;
-    const int slots = (NSTAGE * L.stage_bytes) / slot_bytes;
+    const int slots = min(4, (NSTAGE * L.stage_bytes) / slot_bytes);
     const int pairs = L.n_mt * per_tile;
     if (tid == 0) ok = mbar_wait(bar_p, 0) && ok;
     const uint64_t dPh = sw128_desc(smem_u32(Psm)), dPl = sw128_desc(smem_u32(Psm + 32 * 128));
     int round = 0;
     for (int p0 = 0; p0 < pairs; p0 += slots, ++round) {
       const int np = min(slots, pairs - p0);
-      // Stage np pairs; each is 128 rows x 8 groups of 4 ordinates.
-      for (int it = tid; it < np * kMT * 8; it += kThreads) {
+      // Stage np pairs; each is 128 rows x 8 groups of 4 ordinates.  All of
+      // a thread's loads are issued before any is converted.
+      constexpr int kMaxItems = 16;                        // slots <= 4 -> <= 16 items per thread
+      float4 val[kMaxItems];
+      float bv[kMaxItems];
+#pragma unroll
+      for (int h = 0; h < kMaxItems; ++h) {
+        const int it = tid + h * kThreads;
+        val[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+        bv[h] = 0.f;
+        if (it >= np * kMT * 8) continue;
         const int pp = it / (kMT * 8), rem = it - pp * (kMT * 8);
         const int row = rem >> 3, grp = rem & 7;
         const int p = p0 + pp, t = p / per_tile, r = p - t * per_tile;
         const int i = t * kMT + row, j = t0 + r, m0 = grp * 4;
-        float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-        float bv = 0.f;
         if (i < nx && j < ny && m0 < M) {
           const size_t cell = static_cast<size_t>(j) * nx + i;
-          val = *reinterpret_cast<const float4*>(U + goff + cell * M + m0);
-          bv = __ldg(a.mus + cell);
+          val[h] = *reinterpret_cast<const float4*>(U + goff + cell * M + m0);
+          bv[h] = __ldg(a.mus + cell);
         }
+      }
+#pragma unroll
+      for (int h = 0; h < kMaxItems; ++h) {
+        const int it = tid + h * kThreads;
+        if (it >= np * kMT * 8) continue;
+        const int pp = it / (kMT * 8), rem = it - pp * (kMT * 8);
+        const int row = rem >> 3, grp = rem & 7;
         float4 hi, lo;
-        split4(val, bv, hi, lo);
+        split4(val[h], bv[h], hi, lo);
         unsigned char* slot = sm + pp * slot_bytes;
         const int off = sw128_off(row, grp);
         *reinterpret_cast<float4*>(slot + off) = hi;
@@ -362,23 +376,74 @@ __global__ void __launch_bounds__(kThreads, NSTAGE == 1 ? 2 : 1)
     const int line_step = L.n_mt == 2 ? 1 : 2;
     const int i = t * kMT + 32 * quarter + lane;
     const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * quarter) << 16) + t * kNC;
+    // Per grid row of the slab: the next row's u (M floats of the node) and
+    // a + b are loaded while this row is finished.
+    float4 ucur[8], unext[8];
+    float abcur = 0.f, abnext = 0.f;
+    auto load_row = [&](int rc, float4* u4, float& ab) {
+      const int j = t0 + rc;
+      if (!ok || rc >= per_tile || i >= nx || j >= ny) return;
+      const size_t cell = static_cast<size_t>(j) * nx + i;
+      ab = __ldg(a.mua + cell) + __ldg(a.mus + cell);
+      const float4* up = reinterpret_cast<const float4*>(U + goff + cell * M);
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (4 * k < M) u4[k] = up[k];
+    };
+    // Scattering weights p_k = P~[k][0]; P~[m][q] = p_{(m - q) mod M}
+    // (symmetric circulant), used by the FP32 form of the scattering sum.
+    float pc[MM];
+#pragma unroll
+    for (int k = 0; k < MM; ++k) pc[k] = SCAT_TC ? 0.f : __ldg(a.PT + k);
+    float bcur = 0.f;
+    auto load_b = [&](int rc) {
+      const int j = t0 + rc;
+      return (ok && rc < per_tile && i < nx && j < ny) ? __ldg(a.mus + static_cast<size_t>(j) * nx + i) : 0.f;
+    };
+    load_row(line_first, ucur, abcur);
+    if (!SCAT_TC) bcur = load_b(line_first);
     for (int rc = line_first; rc < per_tile; rc += line_step) {
       const int j = t0 + rc;
-      for (int mh = 0; mh < M; mh += 16) {
-        float acc[16];
-        tmem_ld16(tbase + rc * M + mh, acc);
-        if (!ok || i >= nx || j >= ny) continue;
+      float bnext = 0.f;
+      if (SCAT_TC) {
+        load_row(rc + line_step, unext, abnext);
+      }
+      float acc[MM];
+      tmem_ld16(tbase + rc * M, acc);
+      if (MM > 16) tmem_ld16(tbase + rc * M + 16, acc + 16);
+      if (ok && i < nx && j < ny) {
         const size_t cell = static_cast<size_t>(j) * nx + i;
-        const float ab = __ldg(a.mua + cell) + __ldg(a.mus + cell);
-        const float4* up = reinterpret_cast<const float4*>(U + goff + cell * M + mh);
-        float4* rp = reinterpret_cast<float4*>(R + goff + cell * M + mh);
-        float4 u4[4];
+        float4* rp = reinterpret_cast<float4*>(R + goff + cell * M);
+        if (SCAT_TC) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) u4[k] = up[k];
+          for (int k = 0; k < MM / 4; ++k)
+            rp[k] = make_float4(acc[4 * k] - abcur * ucur[k].x, acc[4 * k + 1] - abcur * ucur[k].y,
+                                acc[4 * k + 2] - abcur * ucur[k].z, acc[4 * k + 3] - abcur * ucur[k].w);
+        } else {
+          float uu[MM];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          rp[k] = make_float4(acc[4 * k] - ab * u4[k].x, acc[4 * k + 1] - ab * u4[k].y,
-                              acc[4 * k + 2] - ab * u4[k].z, acc[4 * k + 3] - ab * u4[k].w);
+          for (int k = 0; k < MM / 4; ++k) {
+            uu[4 * k] = ucur[k].x; uu[4 * k + 1] = ucur[k].y; uu[4 * k + 2] = ucur[k].z; uu[4 * k + 3] = ucur[k].w;
+          }
+#pragma unroll
+          for (int m = 0; m < MM; ++m) {
+            float sc = 0.f;
+#pragma unroll
+            for (int q = 0; q < MM; ++q) sc = fmaf(pc[(m - q + MM) % MM], uu[q], sc);
+            acc[m] = fmaf(bcur, sc, acc[m] - abcur * uu[m]);
+          }
+#pragma unroll
+          for (int k = 0; k < MM / 4; ++k) rp[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+        }
+      }
+      if (SCAT_TC) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) ucur[k] = unext[k];
+        abcur = abnext;
+      } else if (rc + line_step < per_tile) {
+        load_row(rc + line_step, ucur, abcur);
+        bnext = load_b(rc + line_step);
+        bcur = bnext;
       }
     }
   } else {
@@ -558,43 +623,37 @@ __global__ void __launch_bounds__(kThreads, NSTAGE == 1 ? 2 : 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L.tmem_cols));
 }
 
-template <bool XPASS, bool X3, int NSTAGE>
+template <bool XPASS, bool X3, int MM, bool SCAT_TC>
 cudaError_t launch_one(const StepArgs& a, const BoundaryArgs& b, float* U, float* R, const float* L1,
                        const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s) {
+  constexpr int NSTAGE = 1;
   const TcLayout L(XPASS ? a.nx : a.ny, X3);
-  // The y-pass epilogue reuses the stage and P~ regions for 104 KB of buffers.
+  // The y-pass epilogue reuses the stage and P~ regions for its buffers.
   const size_t body = NSTAGE * static_cast<size_t>(L.stage_bytes) + kPBytes;
   const size_t smem = 1024 + (XPASS ? body : (body > kEpiBytes ? body : kEpiBytes));
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(tc_pass_kernel<XPASS, X3, NSTAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         232448 - 2048);
+    cudaFuncSetAttribute(tc_pass_kernel<XPASS, X3, NSTAGE, MM, SCAT_TC>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 232448 - 2048);
     attr = true;
   }
   const int per_tile = kNC / a.M;
   const int lines = XPASS ? a.ny : a.nx;
   dim3 grid((lines + per_tile - 1) / per_tile, 1, a.G);
-  tc_pass_kernel<XPASS, X3, NSTAGE><<<grid, kThreads, smem, s>>>(a, b, U, R, L1, L2, L3, src_step, ring_step);
+  tc_pass_kernel<XPASS, X3, NSTAGE, MM, SCAT_TC><<<grid, kThreads, smem, s>>>(a, b, U, R, L1, L2, L3, src_step,
+                                                                              ring_step);
   return cudaGetLastError();
-}
-
-// One stage and two CTAs per SM (one CTA's epilogue overlaps the other's
-// tensor-core main loop) when RTE_TC_STAGES is unset or 1; two stages and one
-// CTA per SM when it is 2.
-int tc_stages() {
-  static int v = -1;
-  if (v < 0) {
-    const char* e = getenv("RTE_TC_STAGES");
-    v = (e && e[0] == '2') ? 2 : 1;
-  }
-  return v;
 }
 
 template <bool XPASS, bool X3>
 cudaError_t launch_pass(const StepArgs& a, const BoundaryArgs& b, float* U, float* R, const float* L1,
                         const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s) {
-  if (tc_stages() == 2) return launch_one<XPASS, X3, 2>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
-  return launch_one<XPASS, X3, 1>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
+  const bool st = XPASS && a.tc_scatter != 0;
+  if (a.M == 16)
+    return st ? launch_one<XPASS, X3, 16, true>(a, b, U, R, L1, L2, L3, src_step, ring_step, s)
+              : launch_one<XPASS, X3, 16, false>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
+  return st ? launch_one<XPASS, X3, 32, true>(a, b, U, R, L1, L2, L3, src_step, ring_step, s)
+            : launch_one<XPASS, X3, 32, false>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
 }
 
 }  // namespace

@@ -12,12 +12,13 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def gpu_forward(wl, ckpt=0, snaps=None, groups=None, precision=0):
+def gpu_forward(wl, ckpt=0, snaps=None, groups=None, precision=0, flags=0):
     from paper_2202_09421_gb300.solver import FCDOMSolver
     dev = torch.device("cuda:0")
     a = torch.tensor(wl.mua, dtype=torch.float32, device=dev)
     b = torch.tensor(wl.mus, dtype=torch.float32, device=dev)
-    s = FCDOMSolver(wl.grid, wl.optics, a, b, wl.c, wl.dt, ckpt_interval=ckpt, precision=precision)
+    s = FCDOMSolver(wl.grid, wl.optics, a, b, wl.c, wl.dt, ckpt_interval=ckpt, precision=precision,
+                    flags=flags)
     groups = wl.groups if groups is None else groups
     snaps = list(wl.snap_steps) if snaps is None else snaps
     fl = s.forward(groups, wl.n_steps, snaps)

@@ -16,8 +16,8 @@ pytestmark = pytest.mark.gpu
 TF32X3, TF32 = 1, 2
 
 
-def _check(wl, label, precision, tol):
-    s, fl, curves = gpu_forward(wl, precision=precision)
+def _check(wl, label, precision, tol, flags=0):
+    s, fl, curves = gpu_forward(wl, precision=precision, flags=flags)
     c_ref, f_ref, u_ref = oracle_forward(wl)
     ec, ef = rel_l2(curves, c_ref), rel_l2(fl, f_ref)
     print(f"{label} prec {precision}: curves rel L2 {ec:.3e}, fluence rel L2 {ef:.3e}")
@@ -43,6 +43,14 @@ def test_tc_ragged(nx, ny, M, groups):
     L = 1.0 if nx <= 100 else 3.0        # keep dx >= 1/66 cm so that dt = 0.04 ps is stable
     wl = workload_custom(nx, ny, M, 80, 0.04, L=L, mus=20.0, n_groups=groups, t_s=1.0, sigma_t=0.4)
     _check(wl, f"tc ragged{nx}x{ny}_M{M}", TF32X3, 1e-5)
+
+
+@pytest.mark.parametrize("M", [16, 32])
+def test_tc_scattering_contraction_form(M):
+    """RTE_FLAG_TC_SCATTER: the scattering sum as a tcgen05 contraction into
+    the x-pass accumulator meets the same FP32 tolerance."""
+    wl = workload_custom(64, 48, M, 80, 0.04, L=1.0, mus=20.0, n_groups=2, t_s=1.0, sigma_t=0.4)
+    _check(wl, f"tc-scatter M{M}", TF32X3, 1e-5, flags=1)
 
 
 def test_tc_tomo256_truncated():
