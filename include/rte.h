@@ -70,17 +70,23 @@ typedef struct rte_optics {
  * kernel family of the FC operator products:
  *   RTE_PREC_FP32   plain FP32 SIMT kernels (any supported size);
  *   RTE_PREC_TF32X3 tcgen05 tensor cores, split 3xTF32 operands (FP32-level
- *                   accuracy); requires nx, ny <= 256 and M in {16, 32};
+ *                   accuracy); requires M in {16, 32, 64} (nx, ny <= 512);
  *   RTE_PREC_TF32   tcgen05, single TF32 product (reduced precision, same
- *                   size limits).
- * The tensor-core forms synchronise the stream at the end of rte_forward and
- * rte_adjoint_gradient to read their timeout flag (RTE_ERR_TIMEOUT). */
+ *                   size limits);
+ *   RTE_PREC_BF16X3 tcgen05 kind::f16 with BF16 operands split hi + lo, three
+ *                   products (about 2^-16 relative per product);
+ *   RTE_PREC_BF16   tcgen05, single BF16 product.
+ * All tensor-core forms accumulate in FP32.  They synchronise the stream at
+ * the end of rte_forward and rte_adjoint_gradient to read their timeout flag
+ * (RTE_ERR_TIMEOUT). */
 #define RTE_PREC_FP32 0
 #define RTE_PREC_TF32X3 1
 #define RTE_PREC_TF32 2
+#define RTE_PREC_BF16X3 3
+#define RTE_PREC_BF16 4
 /* flags: RTE_FLAG_TC_SCATTER computes the x-pass scattering sum as a tcgen05
  * contraction into the operator accumulator (same operand split as the
- * precision); without it the tensor-core forms evaluate the circulant
+ * precision; TF32 precisions and M <= 32 only, else UNSUPPORTED); without it the tensor-core forms evaluate the circulant
  * scattering sum in FP32 on the CUDA cores of the x-pass epilogue, which
  * measured faster on GB300 (0.158 vs 0.190 ms per x-pass at 256^2, M = 32,
  * 16 groups). */
@@ -126,8 +132,9 @@ typedef struct rte_ctx rte_ctx;
  * cuda_stream is a cudaStream_t (NULL = legacy default stream).
  * dx and dy may differ; each axis gets its own operator.
  * Errors: INVALID_ARG (null pointers, M odd or not a multiple of 8, sizes
- * below 16), UNSUPPORTED (nx or ny above 512, M above 64), UNSTABLE_DT, OOM,
- * CUDA. */
+ * below 16, unknown precision or flags), UNSUPPORTED (nx or ny above 512, M
+ * above 64; a tensor-core precision with M not in {16, 32, 64} or a flag it
+ * does not support), UNSTABLE_DT, OOM, CUDA. */
 rte_status rte_init_medium(rte_ctx** ctx, const rte_grid* grid,
                            const float* mua, const float* mus,
                            const rte_optics* optics, const rte_params* params,

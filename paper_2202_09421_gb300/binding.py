@@ -17,6 +17,8 @@ from .build import LIB
 RTE_PREC_FP32 = 0      # plain FP32 SIMT kernels
 RTE_PREC_TF32X3 = 1    # tcgen05, split 3xTF32 operands (FP32-level accuracy)
 RTE_PREC_TF32 = 2      # tcgen05, one TF32 product (reduced precision)
+RTE_PREC_BF16X3 = 3    # tcgen05 kind::f16, BF16 operands split hi + lo (three products)
+RTE_PREC_BF16 = 4      # tcgen05 kind::f16, one BF16 product
 RTE_FLAG_TC_SCATTER = 1  # x-pass scattering as a tcgen05 contraction
 
 

@@ -32,7 +32,7 @@ struct rte_ctx {
   DevBuf DxT, DyT, PT, xi, eta, mua, mus, area;
   DevBuf face_refl, corner_refl, face_f, corner_f, face_act, corner_act, wexit;
   DevBuf DxImg, DyImg, PImg;       // split, swizzled operators (tensor-core forms)
-  int tc_mode = 0;                 // 0 SIMT FP32, 1 tcgen05 3xTF32, 2 tcgen05 1xTF32
+  int tc_mode = 0;                 // the precision: 0 SIMT FP32, 1-4 tcgen05 forms
   // state of the last forward
   int G = 0, n_steps = -1, kmax = 0;
   int hl = 0;                      // history rotation index
@@ -132,8 +132,8 @@ rte_kern::StepArgs step_args(rte_ctx* c, int G) {
   a.cdt = static_cast<float>(c->opt.c * c->par.dt);
   a.tc_mode = c->tc_mode;
   a.tc_scatter = (c->par.flags & RTE_FLAG_TC_SCATTER) ? 1 : 0;
-  a.DxImg = F(c->DxImg);
-  a.DyImg = F(c->DyImg);
+  a.DxImg = c->DxImg.p;
+  a.DyImg = c->DyImg.p;
   a.PImg = F(c->PImg);
   return a;
 }
@@ -344,9 +344,9 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
   if (!(g->xmax > g->xmin) || !(g->ymax > g->ymin)) return RTE_ERR_INVALID_ARG;
   if (!(p->dt > 0) || !(o->c > 0) || !(o->n_in > 0) || !(o->n_out > 0) || std::fabs(o->g) >= 1.0 ||
       p->ckpt_interval < 0 || (p->flags & ~RTE_FLAG_TC_SCATTER) != 0 ||
-      (p->precision != RTE_PREC_FP32 && p->precision != RTE_PREC_TF32X3 && p->precision != RTE_PREC_TF32))
+      p->precision < RTE_PREC_FP32 || p->precision > RTE_PREC_BF16)
     return RTE_ERR_INVALID_ARG;
-  if (p->precision != RTE_PREC_FP32 && !rte_kern::tc_supported(g->nx, g->ny, g->M))
+  if (p->precision != RTE_PREC_FP32 && !rte_kern::tc_supported(g->nx, g->ny, g->M, p->precision, p->flags))
     return RTE_ERR_UNSUPPORTED;
   rte_ctx* c = new (std::nothrow) rte_ctx();
   if (!c) return RTE_ERR_OOM;
@@ -377,8 +377,14 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
     if (s != RTE_OK) return fail(s);
     if (c->tc_mode != 0) {
       std::vector<float> img;
-      rte_setup::tc_operator_image(Dm, n, img);
-      s = upload(ax == 0 ? c->DxImg : c->DyImg, img, c->stream);
+      std::vector<unsigned short> img16;
+      if (c->tc_mode == RTE_PREC_BF16X3 || c->tc_mode == RTE_PREC_BF16) {
+        rte_setup::tc_operator_image_bf16(Dm, n, img16);
+        s = upload(ax == 0 ? c->DxImg : c->DyImg, img16, c->stream);
+      } else {
+        rte_setup::tc_operator_image(Dm, n, img);
+        s = upload(ax == 0 ? c->DxImg : c->DyImg, img, c->stream);
+      }
       if (s != RTE_OK) return fail(s);
       // the host vector must outlive the asynchronous copy
       s = cuda_status(cudaStreamSynchronize(c->stream));
@@ -412,7 +418,7 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
     }
   rte_status s = RTE_OK;
   std::vector<float> Pimg;
-  if (c->tc_mode != 0) {
+  if (c->tc_mode != 0 && (p->flags & RTE_FLAG_TC_SCATTER)) {
     rte_setup::tc_phase_image(P, g->M, Pimg);
     s = upload(c->PImg, Pimg, c->stream);
   }

@@ -41,11 +41,12 @@ struct StepArgs {
   const float* mus;
   float cdt;                        // c * dt
   // Tensor-core form: 0 = plain FP32 SIMT kernels, 1 = tcgen05 3xTF32,
-  // 2 = tcgen05 1xTF32; DxImg/DyImg hold the split, pre-swizzled operators.
+  // 2 = tcgen05 TF32, 3 = tcgen05 bf16x3, 4 = tcgen05 BF16; DxImg/DyImg hold
+  // the split, pre-swizzled operators (tf32 words or bf16 halves).
   int tc_mode;
   int tc_scatter;                   // x-pass scattering as a tcgen05 contraction
-  const float* DxImg;
-  const float* DyImg;
+  const void* DxImg;
+  const void* DyImg;
   const float* PImg;                // phase matrix as the scattering operand
 };
 
@@ -59,7 +60,7 @@ cudaError_t launch_step(const StepArgs& a, const BoundaryArgs& b, float* U, floa
                         cudaStream_t s, long long* launches, cudaEvent_t* ev = nullptr);
 
 // tcgen05 form of launch_step (a.tc_mode != 0); see rte_tc.cu.
-bool tc_supported(int nx, int ny, int M);
+bool tc_supported(int nx, int ny, int M, int precision, int flags);
 cudaError_t launch_step_tc(const StepArgs& a, const BoundaryArgs& b, float* U, float* R,
                            const float* L1, const float* L2, float* L3, int step,
                            cudaStream_t s, long long* launches, cudaEvent_t* ev);

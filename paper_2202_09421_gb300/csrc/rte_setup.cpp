@@ -98,6 +98,40 @@ void tc_operator_image(const std::vector<double>& D, int n, std::vector<float>& 
       }
 }
 
+// Round an FP32 value to bf16 (8-bit significand), nearest with ties to
+// even, returned as its upper 16 bits.
+static unsigned short bf16_round(float x) {
+  uint32_t b;
+  std::memcpy(&b, &x, 4);
+  if ((b & 0x7f800000u) != 0x7f800000u) b += 0x7fffu + ((b >> 16) & 1u);
+  return static_cast<unsigned short>(b >> 16);
+}
+
+static double bf16_value(unsigned short h) {
+  const uint32_t b = static_cast<uint32_t>(h) << 16;
+  float f;
+  std::memcpy(&f, &b, 4);
+  return f;
+}
+
+void tc_operator_image_bf16(const std::vector<double>& D, int n, std::vector<unsigned short>& img) {
+  const int n_rows = (n + 127) / 128 * 128, n_kc = (n + 63) / 64;
+  img.assign(static_cast<size_t>(n_kc) * 2 * n_rows * 64, 0);
+  for (int q = 0; q < n_kc; ++q)
+    for (int i = 0; i < n; ++i)
+      for (int kk = 0; kk < 64; ++kk) {
+        const int k = q * 64 + kk;
+        if (k >= n) continue;
+        const double v = D[static_cast<size_t>(i) * n + k];
+        const unsigned short hi = bf16_round(static_cast<float>(v));
+        const unsigned short lo = bf16_round(static_cast<float>(v - bf16_value(hi)));
+        const size_t pos = static_cast<size_t>(i) * 64 + (((kk >> 3) ^ (i & 7)) << 3) + (kk & 7);
+        const size_t base = static_cast<size_t>(q) * 2 * n_rows * 64;
+        img[base + pos] = hi;
+        img[base + static_cast<size_t>(n_rows) * 64 + pos] = lo;
+      }
+}
+
 void tc_phase_image(const std::vector<double>& P, int M, std::vector<float>& img) {
   img.assign(2 * 32 * 32, 0.f);
   for (int m = 0; m < M; ++m)

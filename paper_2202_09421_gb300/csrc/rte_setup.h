@@ -25,6 +25,12 @@ void fc_derivative_matrix(int n, double h, double alpha, double beta,
 // lo = tf32(D - hi), zero padding outside n x n.
 void tc_operator_image(const std::vector<double>& D, int n, std::vector<float>& img);
 
+// BF16 form of the same image: chunks of 64 input positions, each a hi then
+// a lo tile of n_rows x 64 bf16 values (value (i, kk) at
+// i*64 + ((kk/8) ^ (i%8))*8 + kk%8); hi = bf16(D), lo = bf16(D - hi), both
+// rounded to nearest even.
+void tc_operator_image_bf16(const std::vector<double>& D, int n, std::vector<unsigned short>& img);
+
 // Same split and swizzle for the phase matrix as the scattering operand:
 // rows m, K = q, 32 x 32 (zero-padded) hi tile then lo tile.
 void tc_phase_image(const std::vector<double>& P, int M, std::vector<float>& img);

@@ -1,16 +1,18 @@
 // Tensor-core (tcgen05) form of the two FC-DOM passes for sm_103a.
 //
 // Each CTA owns one slab tile: 128 slab columns c (x-pass: grid rows j0 ..
-// j0 + 128/M - 1 times the M ordinates; y-pass: grid columns i0 .. times M)
-// over a whole line of n <= 256 positions, K = input positions.
+// j0 + 128/M - 1 times the M ordinates, M in {16, 32, 64}; y-pass: grid
+// columns i0 .. times M) over a whole line of n <= 512 positions, K = input
+// positions.
 //   x-pass: per 128-position tile t of the line, the dense FC operator D
 //     (n x n, Sec. 4.3) is the A operand (M = 128 output positions) and the
 //     transposed slab the B operand (N = 128 slab columns): tensor memory
 //     holds acc_t[lane = output position i][column = (row, m)], so the
 //     epilogue's lanes walk the contiguous x direction of the grid.
 //   y-pass: the slab is the A operand (M = 128 slab columns) and D the B
-//     operand (N = output positions): acc[lane = (column, m)][column = j], so
-//     the epilogue's lanes walk the contiguous (column, m) run of a grid row.
+//     operand (N = output positions, issued as N <= 256 halves):
+//     acc[lane = (column, m)][column = j], so the epilogue's lanes walk the
+//     contiguous (column, m) run of a grid row.
 //
 // x-pass: the node-local scattering sum b P~ u (Sec. 4.1) is accumulated into
 // the same tensor-memory tile as a second contraction: for each grid row r of
@@ -21,19 +23,23 @@
 // (eq. RTEAB4), the Fresnel boundary condition with beam or adjoint
 // injection (eq. RTE), the exitance ring (eq. OpMed), and updates u in place.
 //
-// Precision: kind::tf32 with split operands.  Every operand x is split as
-// hi = tf32(x), lo = tf32(x - hi) (D and P~ on the host, the slab and the
-// scattering operand while staged) and the products hi*hi + hi*lo + lo*hi
-// are accumulated in FP32 (3xTF32, about 2^-22 relative per product); the
-// single-product form (1xTF32) is the reduced-precision variant.
+// Precision: kind::tf32 or kind::f16 (BF16 operands) with split operands.
+// Every operand x is split as hi = r(x), lo = r(x - hi), r the rounding to
+// the operand type (D and P~ on the host, the slab and the scattering operand
+// while staged), and the products hi*hi + hi*lo + lo*hi are accumulated in
+// FP32: 3xTF32 (about 2^-22 relative per product) and bf16x3 (about 2^-16);
+// the single-product forms (TF32, BF16) are the reduced-precision variants.
 //
-// Operands use the K-major 128-byte-swizzle layout (rows of 32 tf32 values;
-// 8-row atoms of 1024 B).  D and P~ chunks are pre-swizzled in global memory
+// Operands use the K-major 128-byte-swizzle layout (rows of 32 tf32 or 64
+// bf16 values; 8-row atoms of 1024 B).  D and P~ chunks are pre-swizzled in global memory
 // and copied with cp.async.bulk; the slab is converted and swizzled by all
-// threads.  K runs in chunks of 32 through a two-stage ring, so chunk q+1 is
-// staged while the tensor core works on chunk q.  One thread issues the MMAs
+// threads.  K runs in chunks of one 128-byte row (32 tf32 / 64 bf16
+// positions); the next chunk's slab values are loaded into registers while
+// the tensor core works on the current one.  One thread issues the MMAs
 // and commits them to mbarriers; every wait is bounded and sets g_tc_error
 // instead of spinning forever.
+#include <cuda_bf16.h>
+
 #include <cstdint>
 
 #include "rte_kernels.cuh"
@@ -46,12 +52,21 @@ namespace {
 
 constexpr int kNC = 128;          // slab columns per tile (MMA N)
 constexpr int kMT = 128;          // output positions per accumulator tile (MMA M)
-constexpr int kKC = 32;           // K per chunk: one 128-byte row of tf32
 constexpr int kThreads = 256;
 constexpr int kTileBytes = 128 * 128;   // one 128-row x 128-byte operand tile
 constexpr long kWaitLimit = 1L << 26;
 constexpr float kAB0 = 55.0f / 24.0f, kAB1 = -59.0f / 24.0f, kAB2 = 37.0f / 24.0f,
                 kAB3 = -9.0f / 24.0f;
+
+// Operand kinds of the precision modes (rte.h): 1 3xTF32, 2 TF32, 3 bf16x3,
+// 4 BF16.  KC = K positions per 128-byte row, GV = values per 16-byte group.
+template <int PREC>
+struct Kind {
+  static constexpr bool BF = PREC == 3 || PREC == 4;
+  static constexpr bool X3 = PREC == 1 || PREC == 3;
+  static constexpr int KC = BF ? 64 : 32;
+  static constexpr int GV = BF ? 8 : 4;
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -64,8 +79,8 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
          (static_cast<uint64_t>(1) << 46) | (static_cast<uint64_t>(2) << 61);
 }
 
-// Byte offset of the 16-byte group grp (4 tf32 values) of row `row` in a
-// K-major 128-byte-swizzle tile.
+// Byte offset of the 16-byte group grp of row `row` in a K-major
+// 128-byte-swizzle tile.
 __device__ __forceinline__ int sw128_off(int row, int grp) { return row * 128 + ((grp ^ (row & 7)) << 4); }
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
@@ -98,12 +113,18 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
       : "memory");
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          tmem),
-      "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+template <bool BF>
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accumulate) {
+  if constexpr (BF)
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+  else
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -136,50 +157,77 @@ __device__ __forceinline__ void split4(float4 v, float s, float4& hi, float4& lo
   hi.w = tf32_rna(s * v.w); lo.w = tf32_rna(s * v.w - hi.w);
 }
 
+// Two bf16 values in one word, the lower K index in the low half.
+__device__ __forceinline__ uint32_t pack_bf16(float k0, float k1) {
+  return static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(k0))) |
+         (static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(k1))) << 16);
+}
+
+// Splits the 8 values s*v[e] of one 16-byte group into bf16 hi and lo words.
+__device__ __forceinline__ void split8_bf16(const float v[8], float s, uint4& hi, uint4& lo) {
+  float h[8], l[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const float x = s * v[e];
+    h[e] = __bfloat162float(__float2bfloat16_rn(x));
+    l[e] = x - h[e];
+  }
+  hi = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
+  lo = make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
+}
+
 struct TcLayout {
-  int n, n_mt, n_kc, stage_bytes, tmem_cols;
-  __host__ __device__ TcLayout(int n_, bool x3) : n(n_) {
+  int n, n_mt, n_kc, nrows_img, stage_bytes, tmem_cols;
+  __host__ __device__ TcLayout(int n_, bool x3, int kc) : n(n_) {
     n_mt = (n + kMT - 1) / kMT;
-    n_kc = (n + kKC - 1) / kKC;
+    n_kc = (n + kc - 1) / kc;
+    nrows_img = n_mt * kMT;
     stage_bytes = (x3 ? 2 : 1) * (n_mt + 1) * kTileBytes;   // D tiles + slab tile, hi (+ lo)
-    tmem_cols = n_mt == 1 ? 128 : 256;
+    tmem_cols = n_mt == 1 ? 128 : n_mt == 2 ? 256 : 512;    // power of two >= n_mt * 128
   }
 };
 
 constexpr int kPBytes = 2 * 32 * 128;   // P~ operand image: hi and lo, 32 rows x 128 B
+constexpr int kMaxM = 64;
 // y-pass epilogue: two 5-array buffers, three [16][128] tiles, boundary tables
-constexpr size_t kEpiBytes = (2 * 5 * 16 + 3 * 16) * 128 * 4 + (8 + 4 + 8) * 32 * 4 + 8 * 32;
+constexpr size_t kEpiBytes = (2 * 5 * 16 + 3 * 16) * 128 * 4 + (8 + 4 + 8) * kMaxM * 4 + 8 * kMaxM;
 
-template <bool XPASS, bool X3, int NSTAGE, int MM, bool SCAT_TC>
-__global__ void __launch_bounds__(kThreads, NSTAGE == 1 ? 2 : 1)
+template <bool XPASS, int PREC, int MM, bool SCAT_TC>
+__global__ void __launch_bounds__(kThreads, MM == 64 ? 1 : 2)
     tc_pass_kernel(StepArgs a, BoundaryArgs b, float* __restrict__ U, float* __restrict__ R,
                    const float* __restrict__ L1, const float* __restrict__ L2, float* __restrict__ L3,
                    int src_step, int ring_step) {
+  using K = Kind<PREC>;
+  constexpr bool X3 = K::X3, BF = K::BF;
+  constexpr int KC = K::KC, GV = K::GV;
   extern __shared__ __align__(1024) unsigned char smraw[];
-  __shared__ __align__(8) uint64_t bars[6];   // full[2], done[2], p_full, scat_done
+  __shared__ __align__(8) uint64_t bars[4];   // full, done, p_full, scat_done
   __shared__ uint32_t tmem_slot;
+  __shared__ float pcs[kMaxM];                 // P~[k][0] (M = 64 epilogue)
   const int nx = a.nx, ny = a.ny;
   constexpr int M = MM;
   const int n = XPASS ? nx : ny;
-  const TcLayout L(n, X3);
-  const int per_tile = kNC / M;               // grid rows (x) or columns (y) per tile
+  const TcLayout L(n, X3, KC);
+  constexpr int per_tile = kNC / M;           // grid rows (x) or columns (y) per tile
   const int g = blockIdx.z;
   const int t0 = blockIdx.x * per_tile;       // first grid row (x) / column (y) of the tile
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const size_t goff = static_cast<size_t>(g) * a.plane;
-  const float* Dimg = XPASS ? a.DxImg : a.DyImg;
+  const unsigned char* Dimg = static_cast<const unsigned char*>(XPASS ? a.DxImg : a.DyImg);
   const float* scale = XPASS ? a.xi : a.eta;
   const int n_lines = XPASS ? ny : nx;        // rows (x) / columns (y) of the grid
 
   unsigned char* sm = smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023);
-  unsigned char* Psm = sm + NSTAGE * L.stage_bytes;     // P~ image (x-pass)
-  const uint32_t bar_full0 = smem_u32(&bars[0]), bar_done0 = smem_u32(&bars[2]);
-  const uint32_t bar_p = smem_u32(&bars[4]), bar_scat = smem_u32(&bars[5]);
+  unsigned char* Psm = sm + L.stage_bytes;    // P~ image (x-pass, TC scattering)
+  const uint32_t bar_full = smem_u32(&bars[0]), bar_done = smem_u32(&bars[1]);
+  const uint32_t bar_p = smem_u32(&bars[2]), bar_scat = smem_u32(&bars[3]);
 
   if (tid == 0) {
-    for (int k = 0; k < 6; ++k) mbar_init(smem_u32(&bars[k]), 1);
+    for (int k = 0; k < 4; ++k) mbar_init(smem_u32(&bars[k]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if (XPASS && MM == 64)
+    for (int k = tid; k < M; k += kThreads) pcs[k] = __ldg(a.PT + k);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(L.tmem_cols));
@@ -189,35 +237,37 @@ __global__ void __launch_bounds__(kThreads, NSTAGE == 1 ? 2 : 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  if (XPASS && tid == 0) bulk_copy(smem_u32(Psm), a.PImg, kPBytes, bar_p);
+  if constexpr (XPASS && SCAT_TC) {
+    if (tid == 0) bulk_copy(smem_u32(Psm), a.PImg, kPBytes, bar_p);
+  }
 
-  const int nrows_img = L.n_mt * kMT;                   // rows of the operator image
-  // idesc: D = F32, A = B = TF32, K-major, M = 128; N = 128 slab columns
-  // (x-pass) or all output positions (y-pass).
-  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) |
-                         (static_cast<uint32_t>((XPASS ? kNC : nrows_img) >> 3) << 17) |
-                         (static_cast<uint32_t>(kMT >> 4) << 24);
-  const size_t chunk_floats = static_cast<size_t>(2) * nrows_img * kKC;
+  const int nrows_img = L.nrows_img;                    // rows of the operator image
+  // idesc: D = F32, A = B = TF32 (2) or BF16 (1), K-major, M = 128; N = 128
+  // slab columns (x-pass) or output positions (y-pass, set per half).
+  constexpr uint32_t kFmt = BF ? 1u : 2u;
+  const uint32_t idesc_base = (1u << 4) | (kFmt << 7) | (kFmt << 10) | (static_cast<uint32_t>(kMT >> 4) << 24);
+  const uint32_t idesc_x = idesc_base | (static_cast<uint32_t>(kNC >> 3) << 17);
+  const size_t chunk_bytes = static_cast<size_t>(2) * nrows_img * 128;   // hi + lo tiles of one K chunk
   bool ok = true;
 
   // ---------------- main loop over K chunks ----------------
   // Slab^T chunk: S[c][kk] = -scale_m u(c, k0 + kk).  Each thread owns 4
-  // (column, 4-value group) items; the next chunk's 16 loads are issued
-  // before this chunk's MMAs so that their latency overlaps the tensor core.
-  constexpr int kItems = kNC * (kKC / 4) / kThreads;   // 4
-  float v[kItems][4];
+  // (column, 16-byte group) items; the next chunk's loads are issued before
+  // this chunk's MMAs so that their latency overlaps the tensor core.
+  constexpr int kItems = kNC * (KC / GV) / kThreads;   // 4
+  float v[kItems][GV];
   auto load_chunk = [&](int q) {
-    const int k0 = q * kKC;
+    const int k0 = q * KC;
 #pragma unroll
     for (int t = 0; t < kItems; ++t) {
       const int it = tid + t * kThreads;
       const int c = it % kNC, grp = it / kNC;
       const int rc = c / M, m = c - rc * M;
       const int line = t0 + rc;
-      const bool valid = rc < per_tile && line < n_lines;
+      const bool valid = line < n_lines;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int k = k0 + grp * 4 + e;
+      for (int e = 0; e < GV; ++e) {
+        const int k = k0 + grp * GV + e;
         v[t][e] = 0.f;
         if (valid && k < n) {
           const size_t idx = XPASS ? goff + (static_cast<size_t>(line) * nx + k) * M + m
@@ -227,34 +277,40 @@ __global__ void __launch_bounds__(kThreads, NSTAGE == 1 ? 2 : 1)
       }
     }
   };
+  unsigned char* Dhi = sm;                                        // n_mt tiles
+  unsigned char* Dlo = sm + L.n_mt * kTileBytes;                  // (split forms)
+  unsigned char* Shi = sm + (X3 ? 2 : 1) * L.n_mt * kTileBytes;
+  unsigned char* Slo = Shi + kTileBytes;
   load_chunk(0);
   for (int q = 0; q < L.n_kc; ++q) {
-    const int s = q % NSTAGE;
-    unsigned char* stage = sm + s * L.stage_bytes;
-    unsigned char* Dhi = stage;                                   // n_mt tiles
-    unsigned char* Dlo = stage + L.n_mt * kTileBytes;             // (3xTF32)
-    unsigned char* Shi = stage + (X3 ? 2 : 1) * L.n_mt * kTileBytes;
-    unsigned char* Slo = Shi + kTileBytes;
-    if (q >= NSTAGE) ok = mbar_wait(bar_done0 + 8 * s, ((q - NSTAGE) / NSTAGE) & 1) && ok;
+    if (q >= 1) ok = mbar_wait(bar_done, (q - 1) & 1) && ok;    // stage free again
     if (tid == 0) {
-      // image chunk: [hi: nrows_img x 32][lo: nrows_img x 32] -> Dhi, Dlo contiguous
-      bulk_copy(smem_u32(Dhi), Dimg + q * chunk_floats, (X3 ? 2 : 1) * nrows_img * 128, bar_full0 + 8 * s);
+      // image chunk: [hi: nrows_img rows][lo: nrows_img rows] -> Dhi, Dlo contiguous
+      bulk_copy(smem_u32(Dhi), Dimg + q * chunk_bytes, (X3 ? 2 : 1) * nrows_img * 128, bar_full);
     }
 #pragma unroll
     for (int t = 0; t < kItems; ++t) {
       const int it = tid + t * kThreads;
       const int c = it % kNC, grp = it / kNC;
-      float4 hi, lo;
-      split4(make_float4(v[t][0], v[t][1], v[t][2], v[t][3]), -__ldg(scale + (c % M)), hi, lo);
+      const float sc = -__ldg(scale + (c % M));
       const int off = sw128_off(c, grp);
-      *reinterpret_cast<float4*>(Shi + off) = hi;
-      if (X3) *reinterpret_cast<float4*>(Slo + off) = lo;
+      if constexpr (BF) {
+        uint4 hi, lo;
+        split8_bf16(v[t], sc, hi, lo);
+        *reinterpret_cast<uint4*>(Shi + off) = hi;
+        if (X3) *reinterpret_cast<uint4*>(Slo + off) = lo;
+      } else {
+        float4 hi, lo;
+        split4(make_float4(v[t][0], v[t][1], v[t][2], v[t][3]), sc, hi, lo);
+        *reinterpret_cast<float4*>(Shi + off) = hi;
+        if (X3) *reinterpret_cast<float4*>(Slo + off) = lo;
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (q + 1 < L.n_kc) load_chunk(q + 1);
     if (tid == 0) {
-      ok = mbar_wait(bar_full0 + 8 * s, (q / NSTAGE) & 1) && ok;
+      ok = mbar_wait(bar_full, q & 1) && ok;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint64_t dSh = sw128_desc(smem_u32(Shi)), dSl = sw128_desc(smem_u32(Slo));
       if (XPASS) {
@@ -263,42 +319,50 @@ __global__ void __launch_bounds__(kThreads, NSTAGE == 1 ? 2 : 1)
           const uint64_t dDl = sw128_desc(smem_u32(Dlo + t * kTileBytes));
           const uint32_t acc_t = tmem + t * kNC;
 #pragma unroll
-          for (int kk = 0; kk < kKC / 8; ++kk) {
+          for (int kk = 0; kk < 4; ++kk) {
             const uint64_t o = static_cast<uint64_t>(kk * 2);   // 32 bytes per K step
-            mma_tf32(acc_t, dDh + o, dSh + o, idesc, (q > 0 || kk > 0) ? 1u : 0u);
+            mma<BF>(acc_t, dDh + o, dSh + o, idesc_x, (q > 0 || kk > 0) ? 1u : 0u);
             if (X3) {
-              mma_tf32(acc_t, dDh + o, dSl + o, idesc, 1u);
-              mma_tf32(acc_t, dDl + o, dSh + o, idesc, 1u);
+              mma<BF>(acc_t, dDh + o, dSl + o, idesc_x, 1u);
+              mma<BF>(acc_t, dDl + o, dSh + o, idesc_x, 1u);
             }
           }
         }
       } else {
-        const uint64_t dDh = sw128_desc(smem_u32(Dhi)), dDl = sw128_desc(smem_u32(Dlo));
+        // N = output positions in halves of at most 256 (rows 256 h .. of D).
+        for (int h = 0; 256 * h < nrows_img; ++h) {
+          const int nh = min(256, nrows_img - 256 * h);
+          const uint32_t idesc_y = idesc_base | (static_cast<uint32_t>(nh >> 3) << 17);
+          const uint64_t dDh = sw128_desc(smem_u32(Dhi + h * 256 * 128));
+          const uint64_t dDl = sw128_desc(smem_u32(Dlo + h * 256 * 128));
+          const uint32_t acc_h = tmem + 256 * h;
 #pragma unroll
-        for (int kk = 0; kk < kKC / 8; ++kk) {
-          const uint64_t o = static_cast<uint64_t>(kk * 2);
-          mma_tf32(tmem, dSh + o, dDh + o, idesc, (q > 0 || kk > 0) ? 1u : 0u);
-          if (X3) {
-            mma_tf32(tmem, dSh + o, dDl + o, idesc, 1u);
-            mma_tf32(tmem, dSl + o, dDh + o, idesc, 1u);
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t o = static_cast<uint64_t>(kk * 2);
+            mma<BF>(acc_h, dSh + o, dDh + o, idesc_y, (q > 0 || kk > 0) ? 1u : 0u);
+            if (X3) {
+              mma<BF>(acc_h, dSh + o, dDl + o, idesc_y, 1u);
+              mma<BF>(acc_h, dSl + o, dDh + o, idesc_y, 1u);
+            }
           }
         }
       }
-      mma_commit(bar_done0 + 8 * s);
+      mma_commit(bar_done);
     }
   }
-  ok = mbar_wait(bar_done0 + 8 * ((L.n_kc - 1) % NSTAGE), ((L.n_kc - 1) / NSTAGE) & 1) && ok;
+  ok = mbar_wait(bar_done, (L.n_kc - 1) & 1) && ok;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   // ---------------- x-pass: scattering contraction into the same tiles ----------------
-  if (XPASS && SCAT_TC) {
+  if constexpr (XPASS && SCAT_TC) {
     // (t, r) pairs: 128 output positions of tile t on grid row j0 + r.  A =
     // b(r, i) u(r, i, q) (K = q padded to 32), B = P~ rows m; N = max(M, 16).
+    // TF32 operands and M <= 32 only.
     const uint32_t idesc_s = (1u << 4) | (2u << 7) | (2u << 10) |
                              (static_cast<uint32_t>((M < 16 ? 16 : M) >> 3) << 17) |
                              (static_cast<uint32_t>(kMT >> 4) << 24);
     const int slot_bytes = (X3 ? 2 : 1) * kTileBytes;
-    const int slots = min(4, (NSTAGE * L.stage_bytes) / slot_bytes);
+    const int slots = min(4, L.stage_bytes / slot_bytes);
     const int pairs = L.n_mt * per_tile;
     if (tid == 0) ok = mbar_wait(bar_p, 0) && ok;
     const uint64_t dPh = sw128_desc(smem_u32(Psm)), dPl = sw128_desc(smem_u32(Psm + 32 * 128));
@@ -350,12 +414,12 @@ __global__ void __launch_bounds__(kThreads, NSTAGE == 1 ? 2 : 1)
           const uint64_t dAh = sw128_desc(smem_u32(slot)), dAl = sw128_desc(smem_u32(slot + kTileBytes));
           const uint32_t acc = tmem + t * kNC + r * M;
 #pragma unroll
-          for (int kk = 0; kk < kKC / 8; ++kk) {
+          for (int kk = 0; kk < 4; ++kk) {
             const uint64_t o = static_cast<uint64_t>(kk * 2);
-            mma_tf32(acc, dAh + o, dPh + o, idesc_s, 1u);
+            mma<false>(acc, dAh + o, dPh + o, idesc_s, 1u);
             if (X3) {
-              mma_tf32(acc, dAh + o, dPl + o, idesc_s, 1u);
-              mma_tf32(acc, dAl + o, dPh + o, idesc_s, 1u);
+              mma<false>(acc, dAh + o, dPl + o, idesc_s, 1u);
+              mma<false>(acc, dAl + o, dPh + o, idesc_s, 1u);
             }
           }
         }
@@ -369,81 +433,129 @@ __global__ void __launch_bounds__(kThreads, NSTAGE == 1 ? 2 : 1)
   // ---------------- epilogues ----------------
   const int quarter = warp & 3;
   if (XPASS) {
-    // lane = output position i, columns = (row, m).  Warps 0-3 take tile 0
-    // and warps 4-7 tile 1; with one tile they split the slab's rows.
-    const int t = L.n_mt == 2 ? (warp >> 2) : 0;
-    const int line_first = L.n_mt == 2 ? 0 : (warp >> 2);
-    const int line_step = L.n_mt == 2 ? 1 : 2;
-    const int i = t * kMT + 32 * quarter + lane;
-    const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * quarter) << 16) + t * kNC;
-    // Per grid row of the slab: the next row's u (M floats of the node) and
-    // a + b are loaded while this row is finished.
-    float4 ucur[8], unext[8];
-    float abcur = 0.f, abnext = 0.f;
-    auto load_row = [&](int rc, float4* u4, float& ab) {
-      const int j = t0 + rc;
-      if (!ok || rc >= per_tile || i >= nx || j >= ny) return;
-      const size_t cell = static_cast<size_t>(j) * nx + i;
-      ab = __ldg(a.mua + cell) + __ldg(a.mus + cell);
-      const float4* up = reinterpret_cast<const float4*>(U + goff + cell * M);
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if (4 * k < M) u4[k] = up[k];
+    // lane = output position i, columns = (row, m).  The (tile t, row rc)
+    // pairs of the CTA, p = t * per_tile + rc, alternate between warps 0-3
+    // and warps 4-7; warp w reads TMEM lanes 32 (w % 4) ...
+    const int half = warp >> 2;
+    const int n_pairs = L.n_mt * per_tile;
+    const uint32_t tq = tmem + (static_cast<uint32_t>(32 * quarter) << 16);
+    auto pair_cell = [&](int p, int& t, int& rc, int& i, int& j) {
+      t = p / per_tile;
+      rc = p - t * per_tile;
+      i = t * kMT + 32 * quarter + lane;
+      j = t0 + rc;
     };
-    // Scattering weights p_k = P~[k][0]; P~[m][q] = p_{(m - q) mod M}
-    // (symmetric circulant), used by the FP32 form of the scattering sum.
-    float pc[MM];
-#pragma unroll
-    for (int k = 0; k < MM; ++k) pc[k] = SCAT_TC ? 0.f : __ldg(a.PT + k);
-    float bcur = 0.f;
-    auto load_b = [&](int rc) {
-      const int j = t0 + rc;
-      return (ok && rc < per_tile && i < nx && j < ny) ? __ldg(a.mus + static_cast<size_t>(j) * nx + i) : 0.f;
-    };
-    load_row(line_first, ucur, abcur);
-    if (!SCAT_TC) bcur = load_b(line_first);
-    for (int rc = line_first; rc < per_tile; rc += line_step) {
-      const int j = t0 + rc;
-      float bnext = 0.f;
-      if (SCAT_TC) {
-        load_row(rc + line_step, unext, abnext);
-      }
-      float acc[MM];
-      tmem_ld16(tbase + rc * M, acc);
-      if (MM > 16) tmem_ld16(tbase + rc * M + 16, acc + 16);
-      if (ok && i < nx && j < ny) {
+    if constexpr (MM == 64) {
+      // 64 ordinates: the node's u and the scattering sums in registers,
+      // P~[k][0] from shared memory (one broadcast value per k).
+      for (int p = half; p < n_pairs; p += 2) {
+        int t, rc, i, j;
+        pair_cell(p, t, rc, i, j);
+        const bool valid = ok && i < nx && j < ny;
         const size_t cell = static_cast<size_t>(j) * nx + i;
+        float uu[MM];
+        float ab = 0.f, bb = 0.f;
+#pragma unroll
+        for (int k = 0; k < MM / 4; ++k) {
+          float4 u4 = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (valid) u4 = reinterpret_cast<const float4*>(U + goff + cell * M)[k];
+          uu[4 * k] = u4.x; uu[4 * k + 1] = u4.y; uu[4 * k + 2] = u4.z; uu[4 * k + 3] = u4.w;
+        }
+        if (valid) {
+          bb = __ldg(a.mus + cell);
+          ab = __ldg(a.mua + cell) + bb;
+        }
+        float sc[MM];
+#pragma unroll
+        for (int m = 0; m < MM; ++m) sc[m] = 0.f;
+#pragma unroll
+        for (int k = 0; k < MM; ++k) {
+          const float pk = pcs[k];
+#pragma unroll
+          for (int m = 0; m < MM; ++m) sc[m] = fmaf(pk, uu[(m - k + MM) % MM], sc[m]);
+        }
         float4* rp = reinterpret_cast<float4*>(R + goff + cell * M);
-        if (SCAT_TC) {
 #pragma unroll
-          for (int k = 0; k < MM / 4; ++k)
-            rp[k] = make_float4(acc[4 * k] - abcur * ucur[k].x, acc[4 * k + 1] - abcur * ucur[k].y,
-                                acc[4 * k + 2] - abcur * ucur[k].z, acc[4 * k + 3] - abcur * ucur[k].w);
-        } else {
-          float uu[MM];
+        for (int gq = 0; gq < MM / 16; ++gq) {
+          float acc[16];
+          tmem_ld16(tq + t * kNC + rc * M + 16 * gq, acc);
+          if (valid) {
 #pragma unroll
-          for (int k = 0; k < MM / 4; ++k) {
-            uu[4 * k] = ucur[k].x; uu[4 * k + 1] = ucur[k].y; uu[4 * k + 2] = ucur[k].z; uu[4 * k + 3] = ucur[k].w;
+            for (int e = 0; e < 4; ++e) {
+              const int m = 16 * gq + 4 * e;
+              rp[m / 4] = make_float4(fmaf(bb, sc[m], acc[4 * e] - ab * uu[m]),
+                                      fmaf(bb, sc[m + 1], acc[4 * e + 1] - ab * uu[m + 1]),
+                                      fmaf(bb, sc[m + 2], acc[4 * e + 2] - ab * uu[m + 2]),
+                                      fmaf(bb, sc[m + 3], acc[4 * e + 3] - ab * uu[m + 3]));
+            }
           }
-#pragma unroll
-          for (int m = 0; m < MM; ++m) {
-            float sc = 0.f;
-#pragma unroll
-            for (int q = 0; q < MM; ++q) sc = fmaf(pc[(m - q + MM) % MM], uu[q], sc);
-            acc[m] = fmaf(bcur, sc, acc[m] - abcur * uu[m]);
-          }
-#pragma unroll
-          for (int k = 0; k < MM / 4; ++k) rp[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
         }
       }
-      if (SCAT_TC) {
+    } else {
+      // Per pair: the node's u (M floats) and a + b; with the tensor-core
+      // scattering the next pair's values are loaded before this one is
+      // finished, otherwise right after it.
+      float4 ucur[MM / 4], unext[MM / 4];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) ucur[k] = unext[k];
-        abcur = abnext;
-      } else if (rc + line_step < per_tile) {
-        load_row(rc + line_step, ucur, abcur);
-        bnext = load_b(rc + line_step);
-        bcur = bnext;
+      for (int k = 0; k < MM / 4; ++k) ucur[k] = unext[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      float abcur = 0.f, abnext = 0.f, bcur = 0.f;
+      auto load_pair = [&](int p, float4* u4, float& ab, float& bv) {
+        int t, rc, i, j;
+        pair_cell(p, t, rc, i, j);
+        if (!ok || p >= n_pairs || i >= nx || j >= ny) return;
+        const size_t cell = static_cast<size_t>(j) * nx + i;
+        bv = __ldg(a.mus + cell);
+        ab = __ldg(a.mua + cell) + bv;
+        const float4* up = reinterpret_cast<const float4*>(U + goff + cell * M);
+#pragma unroll
+        for (int k = 0; k < MM / 4; ++k) u4[k] = up[k];
+      };
+      // Scattering weights p_k = P~[k][0]; P~[m][q] = p_{(m - q) mod M}
+      // (symmetric circulant), used by the FP32 form of the scattering sum.
+      float pc[MM];
+#pragma unroll
+      for (int k = 0; k < MM; ++k) pc[k] = SCAT_TC ? 0.f : __ldg(a.PT + k);
+      load_pair(half, ucur, abcur, bcur);
+      for (int p = half; p < n_pairs; p += 2) {
+        int t, rc, i, j;
+        pair_cell(p, t, rc, i, j);
+        float bdummy = 0.f;
+        if (SCAT_TC) load_pair(p + 2, unext, abnext, bdummy);
+        float acc[MM];
+        tmem_ld16(tq + t * kNC + rc * M, acc);
+        if (MM > 16) tmem_ld16(tq + t * kNC + rc * M + 16, acc + 16);
+        if (ok && i < nx && j < ny) {
+          const size_t cell = static_cast<size_t>(j) * nx + i;
+          float4* rp = reinterpret_cast<float4*>(R + goff + cell * M);
+          if (SCAT_TC) {
+#pragma unroll
+            for (int k = 0; k < MM / 4; ++k)
+              rp[k] = make_float4(acc[4 * k] - abcur * ucur[k].x, acc[4 * k + 1] - abcur * ucur[k].y,
+                                  acc[4 * k + 2] - abcur * ucur[k].z, acc[4 * k + 3] - abcur * ucur[k].w);
+          } else {
+            float uu[MM];
+#pragma unroll
+            for (int k = 0; k < MM / 4; ++k) {
+              uu[4 * k] = ucur[k].x; uu[4 * k + 1] = ucur[k].y; uu[4 * k + 2] = ucur[k].z; uu[4 * k + 3] = ucur[k].w;
+            }
+#pragma unroll
+            for (int m = 0; m < MM; ++m) {
+              float sc = 0.f;
+#pragma unroll
+              for (int q = 0; q < MM; ++q) sc = fmaf(pc[(m - q + MM) % MM], uu[q], sc);
+              acc[m] = fmaf(bcur, sc, acc[m] - abcur * uu[m]);
+            }
+#pragma unroll
+            for (int k = 0; k < MM / 4; ++k) rp[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+          }
+        }
+        if (SCAT_TC) {
+#pragma unroll
+          for (int k = 0; k < MM / 4; ++k) ucur[k] = unext[k];
+          abcur = abnext;
+        } else {
+          load_pair(p + 2, ucur, abcur, bcur);
+        }
       }
     }
   } else {
@@ -454,7 +566,7 @@ __global__ void __launch_bounds__(kThreads, NSTAGE == 1 ? 2 : 1)
     // it copied); warps 0-3 copy the accumulator to a shared [16][128] tile;
     // all threads form AB4 with float4 accesses; boundary nodes are finished
     // from the pre-BC values kept in shared memory.  Uses the stage and P~
-    // regions (104 KB), free after the main loop.
+    // regions, free after the main loop.
     constexpr int kEpiArr = 5;                                   // u, R, L1, L2, L3
     constexpr int kBufFloats = kEpiArr * 16 * kNC;               // 40 KB
     float* ebuf = reinterpret_cast<float*>(sm);                  // [2][5][16][128]
@@ -469,9 +581,9 @@ __global__ void __launch_bounds__(kThreads, NSTAGE == 1 ? 2 : 1)
     const float* srcs[kEpiArr] = {U, R, L1, L2, L3};
     // Boundary tables (faces 0..3, corners 4..7) staged once per CTA.
     float* bc_f = bc_s + 16 * kNC;                               // [8][M]
-    float* bc_wexit = bc_f + 8 * 32;                             // [4][M]
-    int* bc_refl = reinterpret_cast<int*>(bc_wexit + 4 * 32);    // [8][M]
-    unsigned char* bc_act = reinterpret_cast<unsigned char*>(bc_refl + 8 * 32);   // [8][M]
+    float* bc_wexit = bc_f + 8 * kMaxM;                          // [4][M]
+    int* bc_refl = reinterpret_cast<int*>(bc_wexit + 4 * kMaxM); // [8][M]
+    unsigned char* bc_act = reinterpret_cast<unsigned char*>(bc_refl + 8 * kMaxM);   // [8][M]
     for (int e = tid; e < 8 * M; e += kThreads) {
       const int tb = e / M, m = e - tb * M;
       const bool face = tb < 4;
@@ -623,43 +735,66 @@ __global__ void __launch_bounds__(kThreads, NSTAGE == 1 ? 2 : 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L.tmem_cols));
 }
 
-template <bool XPASS, bool X3, int MM, bool SCAT_TC>
+
+template <bool XPASS, int PREC, int MM, bool SCAT_TC>
 cudaError_t launch_one(const StepArgs& a, const BoundaryArgs& b, float* U, float* R, const float* L1,
                        const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s) {
-  constexpr int NSTAGE = 1;
-  const TcLayout L(XPASS ? a.nx : a.ny, X3);
+  using K = Kind<PREC>;
+  const TcLayout L(XPASS ? a.nx : a.ny, K::X3, K::KC);
   // The y-pass epilogue reuses the stage and P~ regions for its buffers.
-  const size_t body = NSTAGE * static_cast<size_t>(L.stage_bytes) + kPBytes;
-  const size_t smem = 1024 + (XPASS ? body : (body > kEpiBytes ? body : kEpiBytes));
+  const size_t body = static_cast<size_t>(L.stage_bytes) + kPBytes;
+  size_t smem = 1024 + (XPASS ? body : (body > kEpiBytes ? body : kEpiBytes));
+  // A CTA holding all 512 TMEM columns keeps the SM to itself, so that a
+  // second resident CTA does not sit in tcgen05.alloc.
+  if (L.tmem_cols == 512 && smem < 120 * 1024) smem = 120 * 1024;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(tc_pass_kernel<XPASS, X3, NSTAGE, MM, SCAT_TC>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, 232448 - 2048);
+    cudaFuncSetAttribute(tc_pass_kernel<XPASS, PREC, MM, SCAT_TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         232448 - 2048);
     attr = true;
   }
-  const int per_tile = kNC / a.M;
+  constexpr int per_tile = kNC / MM;
   const int lines = XPASS ? a.ny : a.nx;
   dim3 grid((lines + per_tile - 1) / per_tile, 1, a.G);
-  tc_pass_kernel<XPASS, X3, NSTAGE, MM, SCAT_TC><<<grid, kThreads, smem, s>>>(a, b, U, R, L1, L2, L3, src_step,
-                                                                              ring_step);
+  tc_pass_kernel<XPASS, PREC, MM, SCAT_TC><<<grid, kThreads, smem, s>>>(a, b, U, R, L1, L2, L3, src_step,
+                                                                        ring_step);
   return cudaGetLastError();
 }
 
-template <bool XPASS, bool X3>
+template <bool XPASS, int PREC>
 cudaError_t launch_pass(const StepArgs& a, const BoundaryArgs& b, float* U, float* R, const float* L1,
                         const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s) {
-  const bool st = XPASS && a.tc_scatter != 0;
+  constexpr bool kScatOk = XPASS && !Kind<PREC>::BF;   // TC scattering: TF32 operands, M <= 32
+  const bool st = kScatOk && a.tc_scatter != 0;
   if (a.M == 16)
-    return st ? launch_one<XPASS, X3, 16, true>(a, b, U, R, L1, L2, L3, src_step, ring_step, s)
-              : launch_one<XPASS, X3, 16, false>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
-  return st ? launch_one<XPASS, X3, 32, true>(a, b, U, R, L1, L2, L3, src_step, ring_step, s)
-            : launch_one<XPASS, X3, 32, false>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
+    return st ? launch_one<XPASS, PREC, 16, kScatOk>(a, b, U, R, L1, L2, L3, src_step, ring_step, s)
+              : launch_one<XPASS, PREC, 16, false>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
+  if (a.M == 32)
+    return st ? launch_one<XPASS, PREC, 32, kScatOk>(a, b, U, R, L1, L2, L3, src_step, ring_step, s)
+              : launch_one<XPASS, PREC, 32, false>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
+  return launch_one<XPASS, PREC, 64, false>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
+}
+
+template <bool XPASS>
+cudaError_t launch_mode(const StepArgs& a, const BoundaryArgs& b, float* U, float* R, const float* L1,
+                        const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s) {
+  switch (a.tc_mode) {
+    case 1: return launch_pass<XPASS, 1>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
+    case 2: return launch_pass<XPASS, 2>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
+    case 3: return launch_pass<XPASS, 3>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
+    default: return launch_pass<XPASS, 4>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
+  }
 }
 
 }  // namespace
 
-bool tc_supported(int nx, int ny, int M) {
-  return nx >= 16 && ny >= 16 && nx <= 256 && ny <= 256 && (M == 16 || M == 32);
+bool tc_supported(int nx, int ny, int M, int precision, int flags) {
+  if (nx < 16 || ny < 16 || nx > 512 || ny > 512) return false;
+  if (M != 16 && M != 32 && M != 64) return false;
+  if (precision < 1 || precision > 4) return false;
+  // The tensor-core scattering contraction exists for TF32 operands and M <= 32.
+  if ((flags & 1) && (precision > 2 || M > 32)) return false;
+  return true;
 }
 
 cudaError_t launch_step_tc(const StepArgs& a, const BoundaryArgs& b, float* U, float* R, const float* L1,
@@ -668,12 +803,10 @@ cudaError_t launch_step_tc(const StepArgs& a, const BoundaryArgs& b, float* U, f
   const int ring_step = b.ring_out ? step : -1;
   cudaError_t e;
   if (ev) cudaEventRecord(ev[0], s);
-  e = a.tc_mode == 2 ? launch_pass<true, false>(a, b, U, R, L1, L2, L3, step, ring_step, s)
-                     : launch_pass<true, true>(a, b, U, R, L1, L2, L3, step, ring_step, s);
+  e = launch_mode<true>(a, b, U, R, L1, L2, L3, step, ring_step, s);
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[1], s);
-  e = a.tc_mode == 2 ? launch_pass<false, false>(a, b, U, R, L1, L2, L3, step, ring_step, s)
-                     : launch_pass<false, true>(a, b, U, R, L1, L2, L3, step, ring_step, s);
+  e = launch_mode<false>(a, b, U, R, L1, L2, L3, step, ring_step, s);
   if (ev) cudaEventRecord(ev[2], s);
   if (launches) *launches += 2;
   return e;
