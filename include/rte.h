@@ -91,6 +91,13 @@ typedef struct rte_optics {
  * measured faster on GB300 (0.158 vs 0.190 ms per x-pass at 256^2, M = 32,
  * 16 groups). */
 #define RTE_FLAG_TC_SCATTER 1
+/* RTE_FLAG_CUDA_GRAPH runs the forward march (rte_forward,
+ * rte_forward_batch) as a CUDA graph: captured on the first call, replayed
+ * while the step count, groups and buffers stay the same, re-captured when
+ * they change.  The graph runs on a private stream ordered after the
+ * context's stream by events, so the call stays asynchronous on that stream.
+ * Off while per-kernel timing is on. */
+#define RTE_FLAG_CUDA_GRAPH 2
 typedef struct rte_params {
   double dt;
   double filter_alpha, filter_beta;
@@ -157,6 +164,23 @@ rte_status rte_forward(rte_ctx* ctx, const rte_source_group* groups, int n_group
                        int n_steps, const int* snap_steps, int n_snaps,
                        float* fluence_out);
 
+/* Batched forward: n_ctx contexts (media of their own grid sizes, at most
+ * 64) advance through n_steps in lockstep, each with its own groups
+ * (groups[i], n_groups[i] entries), exactly as rte_forward without snapshots
+ * would advance each alone; afterwards rte_detector_readout, rte_objective
+ * and rte_adjoint_gradient apply per context.  No counterpart in the paper
+ * beyond its independent forward problems per source (Sec. 2.2); batching
+ * fills the GPU with small media.  The contexts must share M, precision,
+ * flags and stream.  In the tensor-core precisions every step is one x-pass
+ * and one y-pass launch over the tiles of all media (longest lines first);
+ * in RTE_PREC_FP32 each medium launches its own kernels.  Launches are
+ * counted on ctxs[0] (in RTE_PREC_FP32 on each context).  Errors:
+ * INVALID_ARG (also for mixed M, precision,
+ * flags or stream, or a repeated context), OOM, CUDA, TIMEOUT. */
+rte_status rte_forward_batch(rte_ctx* const* ctxs, int n_ctx,
+                             const rte_source_group* const* groups,
+                             const int* n_groups, int n_steps);
+
 /* Detector curves of eq. (OpMed) for the last rte_forward: curves_out
  * (device FP32 [group][det][step]) receives G_j(t = (s + 4) dt) for every
  * step s, from the recorded exitance (trapezoid rule along each face,
@@ -209,8 +233,12 @@ rte_status rte_host_phase_matrix(int M, double g, double exponent, double* P_out
 rte_status rte_set_kernel_timing(rte_ctx* ctx, int on);
 rte_status rte_kernel_times(rte_ctx* ctx, double* ms_out, long long* count_out);
 
-/* Number of kernels this context has launched since creation. */
+/* Number of kernels this context has launched since creation (kernels of
+ * a replayed CUDA graph included). */
 long long rte_kernel_launches(const rte_ctx* ctx);
+
+/* Number of CUDA graphs captured by this context (RTE_FLAG_CUDA_GRAPH). */
+long long rte_graph_captures(const rte_ctx* ctx);
 
 /* Forward solve plus detector curves that allocate no device memory.
  * The paper has no counterpart: this exists for callers that cannot call

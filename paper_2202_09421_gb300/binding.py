@@ -20,6 +20,7 @@ RTE_PREC_TF32 = 2      # tcgen05, one TF32 product (reduced precision)
 RTE_PREC_BF16X3 = 3    # tcgen05 kind::f16, BF16 operands split hi + lo (three products)
 RTE_PREC_BF16 = 4      # tcgen05 kind::f16, one BF16 product
 RTE_FLAG_TC_SCATTER = 1  # x-pass scattering as a tcgen05 contraction
+RTE_FLAG_CUDA_GRAPH = 2  # forward march captured and replayed as a CUDA graph
 
 
 class RteGrid(ctypes.Structure):
@@ -60,7 +61,8 @@ class RTEError(RuntimeError):
 EXPORTS = ("rte_init_medium", "rte_set_medium", "rte_forward", "rte_detector_readout",
            "rte_objective", "rte_adjoint_gradient", "rte_get_state", "rte_kernel_launches",
            "rte_destroy", "rte_status_string", "rte_host_fc_operator", "rte_host_phase_matrix",
-           "rte_set_kernel_timing", "rte_kernel_times", "rte_forward_static")
+           "rte_set_kernel_timing", "rte_kernel_times", "rte_forward_static", "rte_forward_batch",
+           "rte_graph_captures")
 
 _lib = None
 
@@ -92,12 +94,15 @@ def library() -> ctypes.CDLL:
         "rte_set_kernel_timing": [P, c_int],
         "rte_kernel_times": [P, POINTER(c_double), POINTER(c_longlong)],
         "rte_forward_static": [P, POINTER(RteSourceGroup), c_int, c_int, POINTER(RteDetector), c_int, P],
+        "rte_forward_batch": [POINTER(c_void_p), c_int, POINTER(POINTER(RteSourceGroup)), POINTER(c_int), c_int],
+        "rte_graph_captures": [P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = c_int
     lib.rte_kernel_launches.restype = c_longlong
+    lib.rte_graph_captures.restype = c_longlong
     lib.rte_status_string.restype = ctypes.c_char_p
     _lib = lib
     return lib
@@ -169,6 +174,29 @@ def rte_forward(ctx, groups, n_steps: int, snap_steps=(), fluence_out=None):
     snaps = (c_int * max(1, len(snap_steps)))(*snap_steps)
     _check(library().rte_forward(ctx, garr, len(groups), int(n_steps), snaps, len(snap_steps),
                                  _dev_ptr(fluence_out, "fluence_out")), "rte_forward")
+
+
+def rte_forward_batch(ctxs, groups_per_ctx, n_steps: int):
+    """ctxs: list of context handles; groups_per_ctx: one list of groups (each
+    a list of beams) per context."""
+    n = len(ctxs)
+    keep = []
+    garrs = (POINTER(RteSourceGroup) * n)()
+    ngr = (c_int * n)()
+    for i, groups in enumerate(groups_per_ctx):
+        beam_arrays = [make_beams(bl) for bl in groups]
+        garr = (RteSourceGroup * len(groups))()
+        for k, bl in enumerate(groups):
+            garr[k] = RteSourceGroup(ctypes.cast(beam_arrays[k], POINTER(RteBeam)), len(bl))
+        keep.append((beam_arrays, garr))
+        garrs[i] = ctypes.cast(garr, POINTER(RteSourceGroup))
+        ngr[i] = len(groups)
+    carr = (c_void_p * n)(*[c.value for c in ctxs])
+    _check(library().rte_forward_batch(carr, n, garrs, ngr, int(n_steps)), "rte_forward_batch")
+
+
+def rte_graph_captures(ctx) -> int:
+    return int(library().rte_graph_captures(ctx))
 
 
 def rte_detector_readout(ctx, dets, curves_out):

@@ -1,6 +1,7 @@
 // C ABI of the FC-DOM library (include/rte.h): context, set-up uploads, the
 // time-march driver, detector readout and the checkpointed adjoint gradient.
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -46,6 +47,18 @@ struct rte_ctx {
   size_t n_timed = 0;
   // adjoint scratch
   DevBuf MU, RA, LA[3], seg, curves64, resid, partial, Jdev, rho, grad_a, grad_b, Wd, Wn, lohi;
+  // batched forward: device copy of the problem table
+  DevBuf batch_tab;
+  // CUDA-graph form of the forward march (RTE_FLAG_CUDA_GRAPH): the graph is
+  // captured and replayed on a private stream ordered after the context's
+  // stream by events, and re-captured when its key (sizes and every buffer
+  // it touches) changes.
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev[2] = {nullptr, nullptr};
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<unsigned long long> gkey;
+  long long glaunches = 0;         // kernels per replay
+  long long graph_captures = 0;
 };
 
 namespace {
@@ -247,6 +260,141 @@ rte_status tc_check(rte_ctx* c) {
   return flag ? RTE_ERR_TIMEOUT : RTE_OK;
 }
 
+// Validates the beams and sets up a forward march of n_steps on G = n_groups
+// groups: state buffers, checkpoint store, source factors, zero state.
+rte_status prepare_forward(rte_ctx* c, const rte_source_group* groups, int n_groups, int n_steps) {
+  int kmax = 0;
+  for (int g = 0; g < n_groups; ++g) {
+    if (groups[g].n_beams < 0 || (groups[g].n_beams > 0 && !groups[g].beams)) return RTE_ERR_INVALID_ARG;
+    for (int k = 0; k < groups[g].n_beams; ++k) {
+      const rte_beam& bm = groups[g].beams[k];
+      if (!(bm.sigma_x > 0) || !(bm.sigma_theta > 0) || !(bm.sigma_t > 0)) return RTE_ERR_INVALID_ARG;
+    }
+    kmax = std::max(kmax, groups[g].n_beams);
+  }
+  const int G = n_groups;
+  const size_t gbytes = static_cast<size_t>(G) * c->plane * sizeof(float);
+  RTE_TRY(ensure(c->U, gbytes));
+  RTE_TRY(ensure(c->R, gbytes));
+  for (int q = 0; q < 3; ++q) RTE_TRY(ensure(c->L[q], gbytes));
+  RTE_TRY(ensure(c->ring, static_cast<size_t>(G) * n_steps * c->ring_len * sizeof(float)));
+  const int I = c->par.ckpt_interval;
+  c->n_ckpt = I > 0 ? (n_steps + I - 1) / I : 0;
+  if (I > 0) RTE_TRY(ensure(c->ckpt, static_cast<size_t>(c->n_ckpt) * 4 * gbytes));
+
+  // Source factors q = S(node) A(m) T(step) per beam (eq. RTEsources2).
+  const int kk = std::max(kmax, 1);
+  std::vector<float> S(static_cast<size_t>(G) * kk * c->ring_len, 0.f),
+      A(static_cast<size_t>(G) * kk * c->M, 0.f), T(static_cast<size_t>(G) * kk * n_steps, 0.f);
+  for (int g = 0; g < G; ++g)
+    for (int k = 0; k < groups[g].n_beams; ++k) {
+      const rte_beam& bm = groups[g].beams[k];
+      const size_t gk = static_cast<size_t>(g) * kk + k;
+      for (int nd = 0; nd < c->ring_len; ++nd) {
+        const double dx = c->ring_x[nd] - bm.x, dy = c->ring_y[nd] - bm.y;
+        S[gk * c->ring_len + nd] = static_cast<float>(std::exp(-(dx * dx + dy * dy) / (2.0 * bm.sigma_x * bm.sigma_x)));
+      }
+      for (int m = 0; m < c->M; ++m)
+        A[gk * c->M + m] = static_cast<float>(
+            bm.amplitude * rte_setup::window(angdist(2.0 * kPi * m / c->M, bm.theta) / bm.sigma_theta));
+      for (int s = 0; s < n_steps; ++s)
+        T[gk * n_steps + s] = static_cast<float>(temporal(bm, (s + 4) * c->par.dt));
+    }
+  RTE_TRY(upload(c->S, S, c->stream));
+  RTE_TRY(upload(c->A, A, c->stream));
+  RTE_TRY(upload(c->T, T, c->stream));
+  c->kmax = kmax;
+  c->G = G;
+  c->n_steps = n_steps;
+
+  RTE_TRY(cuda_status(cudaMemsetAsync(c->U.p, 0, gbytes, c->stream)));
+  for (int q = 0; q < 3; ++q) RTE_TRY(cuda_status(cudaMemsetAsync(c->L[q].p, 0, gbytes, c->stream)));
+  c->hl = 0;
+  return RTE_OK;
+}
+
+// Boundary arguments of the forward march set up by prepare_forward.
+rte_kern::BoundaryArgs forward_bargs(rte_ctx* c) {
+  rte_kern::BoundaryArgs b = boundary_args(c);
+  b.S = F(c->S); b.A = F(c->A); b.T = F(c->T); b.kmax = c->kmax; b.T_len = c->n_steps;
+  b.ring_out = F(c->ring); b.ring_steps = c->n_steps;
+  return b;
+}
+
+// Checkpoint of the march state before step s (every ckpt_interval steps).
+rte_status save_checkpoint(rte_ctx* c, int s, int hl) {
+  const int I = c->par.ckpt_interval;
+  if (I <= 0 || s % I != 0) return RTE_OK;
+  const size_t gbytes = static_cast<size_t>(c->G) * c->plane * sizeof(float);
+  char* base = static_cast<char*>(c->ckpt.p) + static_cast<size_t>(s / I) * 4 * gbytes;
+  const void* src[4] = {c->U.p, c->L[hl].p, c->L[(hl + 1) % 3].p, c->L[(hl + 2) % 3].p};
+  for (int q = 0; q < 4; ++q)
+    RTE_TRY(cuda_status(cudaMemcpyAsync(base + q * gbytes, src[q], gbytes, cudaMemcpyDeviceToDevice, c->stream)));
+  return RTE_OK;
+}
+
+// Runs `enqueue` (which puts the whole march on c->stream) directly, or, in
+// the CUDA-graph form, replays the graph captured from it (capturing it when
+// `key` differs from the cached one).  The kernel launch counter counts the
+// replayed kernels.
+template <class Fn>
+rte_status run_march(rte_ctx* c, const std::vector<unsigned long long>& key, Fn&& enqueue) {
+  if (!(c->par.flags & RTE_FLAG_CUDA_GRAPH) || c->timing) return enqueue();
+  if (!c->gstream) {
+    RTE_TRY(cuda_status(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking)));
+    for (int k = 0; k < 2; ++k)
+      RTE_TRY(cuda_status(cudaEventCreateWithFlags(&c->gev[k], cudaEventDisableTiming)));
+  }
+  if (!c->gexec || key != c->gkey) {
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+    const cudaStream_t user = c->stream;
+    const long long l0 = c->launches;
+    c->stream = c->gstream;
+    cudaGraph_t graph = nullptr;
+    rte_status st = cuda_status(cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+    if (st == RTE_OK) {
+      st = enqueue();
+      const cudaError_t e = cudaStreamEndCapture(c->gstream, &graph);
+      if (st == RTE_OK) st = cuda_status(e);
+    }
+    c->stream = user;
+    c->glaunches = c->launches - l0;
+    c->launches = l0;
+    if (st == RTE_OK) st = cuda_status(cudaGraphInstantiate(&c->gexec, graph, 0));
+    if (graph) cudaGraphDestroy(graph);
+    if (st != RTE_OK) {
+      c->gexec = nullptr;
+      return st;
+    }
+    c->gkey = key;
+    ++c->graph_captures;
+  }
+  RTE_TRY(cuda_status(cudaEventRecord(c->gev[0], c->stream)));
+  RTE_TRY(cuda_status(cudaStreamWaitEvent(c->gstream, c->gev[0], 0)));
+  RTE_TRY(cuda_status(cudaGraphLaunch(c->gexec, c->gstream)));
+  RTE_TRY(cuda_status(cudaEventRecord(c->gev[1], c->gstream)));
+  RTE_TRY(cuda_status(cudaStreamWaitEvent(c->stream, c->gev[1], 0)));
+  c->launches += c->glaunches;
+  return RTE_OK;
+}
+
+unsigned long long key_ptr(const void* p) { return static_cast<unsigned long long>(reinterpret_cast<uintptr_t>(p)); }
+
+// Key of the buffers a forward march of context c touches.
+void append_forward_key(const rte_ctx* c, std::vector<unsigned long long>& key) {
+  const void* ptrs[] = {c->U.p, c->R.p, c->L[0].p, c->L[1].p, c->L[2].p, c->ring.p, c->S.p, c->A.p,
+                        c->T.p, c->ckpt.p, c->mua.p, c->mus.p};
+  key.push_back(static_cast<unsigned long long>(c->n_steps));
+  key.push_back(static_cast<unsigned long long>(c->G));
+  key.push_back(static_cast<unsigned long long>(c->kmax));
+  for (const void* p : ptrs) key.push_back(key_ptr(p));
+}
+
+constexpr int kMaxBatch = 64;
+
 }  // namespace
 
 extern "C" {
@@ -266,6 +414,8 @@ const char* rte_status_string(rte_status s) {
 }
 
 long long rte_kernel_launches(const rte_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+long long rte_graph_captures(const rte_ctx* ctx) { return ctx ? ctx->graph_captures : -1; }
 
 rte_status rte_set_kernel_timing(rte_ctx* c, int on) {
   if (!c) return RTE_ERR_INVALID_ARG;
@@ -319,7 +469,15 @@ rte_status rte_destroy(rte_ctx* c) {
                    &c->Jdev, &c->rho, &c->grad_a, &c->grad_b, &c->Wd, &c->Wn, &c->lohi,
                    &c->DxImg, &c->DyImg, &c->PImg};
   for (DevBuf* b : all) release(*b);
+  release(c->batch_tab);
   for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (cudaEvent_t e : c->gev)
+    if (e) cudaEventDestroy(e);
+  if (c->gstream) {
+    cudaStreamSynchronize(c->gstream);
+    cudaStreamDestroy(c->gstream);
+  }
   delete c;
   return RTE_OK;
 }
@@ -343,7 +501,7 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
   if (g->nx > 512 || g->ny > 512 || g->M > 64) return RTE_ERR_UNSUPPORTED;
   if (!(g->xmax > g->xmin) || !(g->ymax > g->ymin)) return RTE_ERR_INVALID_ARG;
   if (!(p->dt > 0) || !(o->c > 0) || !(o->n_in > 0) || !(o->n_out > 0) || std::fabs(o->g) >= 1.0 ||
-      p->ckpt_interval < 0 || (p->flags & ~RTE_FLAG_TC_SCATTER) != 0 ||
+      p->ckpt_interval < 0 || (p->flags & ~(RTE_FLAG_TC_SCATTER | RTE_FLAG_CUDA_GRAPH)) != 0 ||
       p->precision < RTE_PREC_FP32 || p->precision > RTE_PREC_BF16)
     return RTE_ERR_INVALID_ARG;
   if (p->precision != RTE_PREC_FP32 && !rte_kern::tc_supported(g->nx, g->ny, g->M, p->precision, p->flags))
@@ -450,58 +608,103 @@ rte_status rte_forward(rte_ctx* c, const rte_source_group* groups, int n_groups,
       return RTE_ERR_INVALID_ARG;
     snap_index[snap_steps[k]] = k;
   }
-  int kmax = 0;
-  for (int g = 0; g < n_groups; ++g) {
-    if (groups[g].n_beams < 0 || (groups[g].n_beams > 0 && !groups[g].beams)) return RTE_ERR_INVALID_ARG;
-    for (int k = 0; k < groups[g].n_beams; ++k) {
-      const rte_beam& bm = groups[g].beams[k];
-      if (!(bm.sigma_x > 0) || !(bm.sigma_theta > 0) || !(bm.sigma_t > 0)) return RTE_ERR_INVALID_ARG;
-    }
-    kmax = std::max(kmax, groups[g].n_beams);
-  }
-  const int G = n_groups;
-  const size_t gbytes = static_cast<size_t>(G) * c->plane * sizeof(float);
-  RTE_TRY(ensure(c->U, gbytes));
-  RTE_TRY(ensure(c->R, gbytes));
-  for (int q = 0; q < 3; ++q) RTE_TRY(ensure(c->L[q], gbytes));
-  RTE_TRY(ensure(c->ring, static_cast<size_t>(G) * n_steps * c->ring_len * sizeof(float)));
-  const int I = c->par.ckpt_interval;
-  c->n_ckpt = I > 0 ? (n_steps + I - 1) / I : 0;
-  if (I > 0) RTE_TRY(ensure(c->ckpt, static_cast<size_t>(c->n_ckpt) * 4 * gbytes));
-
-  // Source factors q = S(node) A(m) T(step) per beam (eq. RTEsources2).
-  const int kk = std::max(kmax, 1);
-  std::vector<float> S(static_cast<size_t>(G) * kk * c->ring_len, 0.f),
-      A(static_cast<size_t>(G) * kk * c->M, 0.f), T(static_cast<size_t>(G) * kk * n_steps, 0.f);
-  for (int g = 0; g < G; ++g)
-    for (int k = 0; k < groups[g].n_beams; ++k) {
-      const rte_beam& bm = groups[g].beams[k];
-      const size_t gk = static_cast<size_t>(g) * kk + k;
-      for (int nd = 0; nd < c->ring_len; ++nd) {
-        const double dx = c->ring_x[nd] - bm.x, dy = c->ring_y[nd] - bm.y;
-        S[gk * c->ring_len + nd] = static_cast<float>(std::exp(-(dx * dx + dy * dy) / (2.0 * bm.sigma_x * bm.sigma_x)));
-      }
-      for (int m = 0; m < c->M; ++m)
-        A[gk * c->M + m] = static_cast<float>(
-            bm.amplitude * rte_setup::window(angdist(2.0 * kPi * m / c->M, bm.theta) / bm.sigma_theta));
-      for (int s = 0; s < n_steps; ++s)
-        T[gk * n_steps + s] = static_cast<float>(temporal(bm, (s + 4) * c->par.dt));
-    }
-  RTE_TRY(upload(c->S, S, c->stream));
-  RTE_TRY(upload(c->A, A, c->stream));
-  RTE_TRY(upload(c->T, T, c->stream));
-  c->kmax = kmax;
-  c->G = G;
-  c->n_steps = n_steps;
-
-  RTE_TRY(cuda_status(cudaMemsetAsync(c->U.p, 0, gbytes, c->stream)));
-  for (int q = 0; q < 3; ++q) RTE_TRY(cuda_status(cudaMemsetAsync(c->L[q].p, 0, gbytes, c->stream)));
-  c->hl = 0;
-  rte_kern::BoundaryArgs b = boundary_args(c);
-  b.S = F(c->S); b.A = F(c->A); b.T = F(c->T); b.kmax = kmax; b.T_len = n_steps;
-  b.ring_out = F(c->ring); b.ring_steps = n_steps;
-  RTE_TRY(march(c, c->U, c->R, c->L, c->hl, G, 0, n_steps, b, true, snap_index, fluence_out, nullptr));
+  RTE_TRY(prepare_forward(c, groups, n_groups, n_steps));
+  const rte_kern::BoundaryArgs b = forward_bargs(c);
+  std::vector<unsigned long long> key;
+  append_forward_key(c, key);
+  key.push_back(key_ptr(fluence_out));
+  for (int k = 0; k < n_snaps; ++k) key.push_back(static_cast<unsigned long long>(snap_steps[k]));
+  RTE_TRY(run_march(c, key, [&]() {
+    int hl = 0;
+    return march(c, c->U, c->R, c->L, hl, c->G, 0, n_steps, b, true, snap_index, fluence_out, nullptr);
+  }));
+  c->hl = (2 * n_steps) % 3;
   return tc_check(c);
+}
+
+rte_status rte_forward_batch(rte_ctx* const* ctxs, int n_ctx, const rte_source_group* const* groups,
+                             const int* n_groups, int n_steps) {
+  if (!ctxs || n_ctx <= 0 || n_ctx > kMaxBatch || !groups || !n_groups || n_steps <= 0)
+    return RTE_ERR_INVALID_ARG;
+  rte_ctx* c0 = ctxs[0];
+  for (int i = 0; i < n_ctx; ++i) {
+    rte_ctx* c = ctxs[i];
+    if (!c || !groups[i] || n_groups[i] <= 0) return RTE_ERR_INVALID_ARG;
+    if (c->M != c0->M || c->tc_mode != c0->tc_mode || c->par.flags != c0->par.flags || c->stream != c0->stream)
+      return RTE_ERR_INVALID_ARG;
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == c) return RTE_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < n_ctx; ++i) RTE_TRY(prepare_forward(ctxs[i], groups[i], n_groups[i], n_steps));
+  std::vector<unsigned long long> key{static_cast<unsigned long long>(n_ctx)};
+  for (int i = 0; i < n_ctx; ++i) {
+    key.push_back(key_ptr(ctxs[i]));
+    append_forward_key(ctxs[i], key);
+  }
+  const std::vector<int> no_snaps(n_steps, -1);
+  std::vector<rte_kern::BoundaryArgs> bargs(n_ctx);
+  for (int i = 0; i < n_ctx; ++i) bargs[i] = forward_bargs(ctxs[i]);
+  if (c0->tc_mode == 0) {
+    // Plain FP32 form: every medium's kernels, in lockstep.
+    RTE_TRY(run_march(c0, key, [&]() {
+      std::vector<int> hl(n_ctx, 0);
+      for (int s = 0; s < n_steps; ++s)
+        for (int i = 0; i < n_ctx; ++i) {
+          rte_ctx* c = ctxs[i];
+          const cudaStream_t keep = c->stream;
+          c->stream = c0->stream;              // the capture stream while a graph is recorded
+          const rte_status st = march(c, c->U, c->R, c->L, hl[i], c->G, s, s + 1, bargs[i], true, no_snaps,
+                                      nullptr, nullptr);
+          c->stream = keep;
+          if (st != RTE_OK) return st;
+        }
+      return RTE_OK;
+    }));
+  } else {
+    // Tensor-core form: one x-pass and one y-pass launch per step over the
+    // tiles of every medium, the media with the longest lines first.
+    std::vector<int> order(n_ctx);
+    for (int i = 0; i < n_ctx; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      return std::max(ctxs[x]->nx, ctxs[x]->ny) > std::max(ctxs[y]->nx, ctxs[y]->ny);
+    });
+    std::vector<rte_kern::BatchProblem> tab(n_ctx);
+    for (int r = 0; r < n_ctx; ++r) {
+      rte_ctx* c = ctxs[order[r]];
+      rte_kern::BatchProblem& P = tab[r];
+      P.a = step_args(c, c->G);
+      P.b = bargs[order[r]];
+      P.U = F(c->U);
+      P.R = F(c->R);
+      for (int q = 0; q < 3; ++q) P.L[q] = F(c->L[q]);
+    }
+    int ctas_x = 0, ctas_y = 0;
+    rte_kern::tc_batch_layout(tab.data(), n_ctx, &ctas_x, &ctas_y);
+    RTE_TRY(upload(c0->batch_tab, tab, c0->stream));
+    // the table must reach the device before the host vector goes away
+    RTE_TRY(cuda_status(cudaStreamSynchronize(c0->stream)));
+    key.push_back(key_ptr(c0->batch_tab.p));
+    const auto* dev = static_cast<const rte_kern::BatchProblem*>(c0->batch_tab.p);
+    RTE_TRY(run_march(c0, key, [&]() {
+      int hl = 0;
+      for (int s = 0; s < n_steps; ++s) {
+        for (int i = 0; i < n_ctx; ++i) {
+          rte_ctx* c = ctxs[i];
+          const cudaStream_t keep = c->stream;
+          c->stream = c0->stream;
+          const rte_status st = save_checkpoint(c, s, hl);
+          c->stream = keep;
+          if (st != RTE_OK) return st;
+        }
+        RTE_TRY(cuda_status(rte_kern::launch_step_tc_batched(tab.data(), dev, n_ctx, s, hl, c0->stream,
+                                                              &c0->launches)));
+        hl = (hl + 2) % 3;
+      }
+      return RTE_OK;
+    }));
+  }
+  for (int i = 0; i < n_ctx; ++i) ctxs[i]->hl = (2 * n_steps) % 3;
+  return tc_check(c0);
 }
 
 rte_status rte_detector_readout(rte_ctx* c, const rte_detector* dets, int n_det, float* curves_out) {

@@ -59,11 +59,30 @@ cudaError_t launch_step(const StepArgs& a, const BoundaryArgs& b, float* U, floa
                         const float* L1, const float* L2, float* L3, int step,
                         cudaStream_t s, long long* launches, cudaEvent_t* ev = nullptr);
 
+// One medium of a batched step: its step and boundary arguments, its state
+// buffers, and the CTA ranges of its tiles in the batched x- and y-pass
+// launches (tiles_x = row tiles per group, tiles_y = column tiles per group).
+struct BatchProblem {
+  StepArgs a;
+  BoundaryArgs b;
+  float* U;
+  float* R;
+  float* L[3];
+  int tile0_x, tiles_x, tile0_y, tiles_y;
+};
+
 // tcgen05 form of launch_step (a.tc_mode != 0); see rte_tc.cu.
 bool tc_supported(int nx, int ny, int M, int precision, int flags);
 cudaError_t launch_step_tc(const StepArgs& a, const BoundaryArgs& b, float* U, float* R,
                            const float* L1, const float* L2, float* L3, int step,
                            cudaStream_t s, long long* launches, cudaEvent_t* ev);
+// Fills the CTA ranges of the problems (in order) and returns the launch
+// sizes; every problem must share M, tc_mode and tc_scatter.
+void tc_batch_layout(BatchProblem* probs, int n, int* ctas_x, int* ctas_y);
+// One AB4 step of every problem with one x-pass and one y-pass launch;
+// probs_dev is a device copy of the host table `probs`.
+cudaError_t launch_step_tc_batched(const BatchProblem* probs, const BatchProblem* probs_dev, int n,
+                                   int step, int hl, cudaStream_t s, long long* launches);
 // Reads and clears the tcgen05 kernels' bounded-wait timeout flag
 // (synchronous).
 cudaError_t tc_take_error(int* flag);

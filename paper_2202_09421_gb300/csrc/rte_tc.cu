@@ -192,11 +192,14 @@ constexpr int kMaxM = 64;
 // y-pass epilogue: two 5-array buffers, three [16][128] tiles, boundary tables
 constexpr size_t kEpiBytes = (2 * 5 * 16 + 3 * 16) * 128 * 4 + (8 + 4 + 8) * kMaxM * 4 + 8 * kMaxM;
 
+// One CTA's work on slab tile `tile` of group g (x-pass: grid rows
+// tile * 128/M ...; y-pass: grid columns).  Shared by the single-medium and
+// the batched kernels below.
 template <bool XPASS, int PREC, int MM, bool SCAT_TC>
-__global__ void __launch_bounds__(kThreads, MM == 64 ? 1 : 2)
-    tc_pass_kernel(StepArgs a, BoundaryArgs b, float* __restrict__ U, float* __restrict__ R,
-                   const float* __restrict__ L1, const float* __restrict__ L2, float* __restrict__ L3,
-                   int src_step, int ring_step) {
+__device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryArgs& b, float* __restrict__ U,
+                                             float* __restrict__ R, const float* __restrict__ L1,
+                                             const float* __restrict__ L2, float* __restrict__ L3, int src_step,
+                                             int ring_step, int tile, int g) {
   using K = Kind<PREC>;
   constexpr bool X3 = K::X3, BF = K::BF;
   constexpr int KC = K::KC, GV = K::GV;
@@ -209,8 +212,7 @@ __global__ void __launch_bounds__(kThreads, MM == 64 ? 1 : 2)
   const int n = XPASS ? nx : ny;
   const TcLayout L(n, X3, KC);
   constexpr int per_tile = kNC / M;           // grid rows (x) or columns (y) per tile
-  const int g = blockIdx.z;
-  const int t0 = blockIdx.x * per_tile;       // first grid row (x) / column (y) of the tile
+  const int t0 = tile * per_tile;             // first grid row (x) / column (y) of the tile
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const size_t goff = static_cast<size_t>(g) * a.plane;
   const unsigned char* Dimg = static_cast<const unsigned char*>(XPASS ? a.DxImg : a.DyImg);
@@ -735,6 +737,39 @@ __global__ void __launch_bounds__(kThreads, MM == 64 ? 1 : 2)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L.tmem_cols));
 }
 
+template <bool XPASS, int PREC, int MM, bool SCAT_TC>
+__global__ void __launch_bounds__(kThreads, MM == 64 ? 1 : 2)
+    tc_pass_kernel(StepArgs a, BoundaryArgs b, float* __restrict__ U, float* __restrict__ R,
+                   const float* __restrict__ L1, const float* __restrict__ L2, float* __restrict__ L3,
+                   int src_step, int ring_step) {
+  tc_pass_body<XPASS, PREC, MM, SCAT_TC>(a, b, U, R, L1, L2, L3, src_step, ring_step, blockIdx.x, blockIdx.z);
+}
+
+// Batched form: the CTAs of one launch cover the tiles of several media
+// (problems sorted by first CTA index); each CTA copies its problem's
+// descriptor to shared memory and runs the same body.  The history ring of
+// every problem is at the same rotation hl (the problems step in lockstep).
+template <bool XPASS, int PREC, int MM, bool SCAT_TC>
+__global__ void __launch_bounds__(kThreads, MM == 64 ? 1 : 2)
+    tc_pass_batched(const BatchProblem* __restrict__ probs, int n_probs, int step, int hl) {
+  __shared__ BatchProblem sp;
+  __shared__ int sp_tile, sp_g;
+  if (threadIdx.x == 0) {
+    const int bid = blockIdx.x;
+    int p = 0;
+    while (p + 1 < n_probs && bid >= (XPASS ? probs[p + 1].tile0_x : probs[p + 1].tile0_y)) ++p;
+    sp = probs[p];
+    const int local = bid - (XPASS ? sp.tile0_x : sp.tile0_y);
+    const int tiles = XPASS ? sp.tiles_x : sp.tiles_y;
+    sp_g = local / tiles;
+    sp_tile = local - sp_g * tiles;
+  }
+  __syncthreads();
+  const int h1 = hl, h2 = (hl + 1) % 3, h3 = (hl + 2) % 3;
+  tc_pass_body<XPASS, PREC, MM, SCAT_TC>(sp.a, sp.b, sp.U, sp.R, sp.L[h1], sp.L[h2], sp.L[h3], step,
+                                         sp.b.ring_out ? step : -1, sp_tile, sp_g);
+}
+
 
 template <bool XPASS, int PREC, int MM, bool SCAT_TC>
 cudaError_t launch_one(const StepArgs& a, const BoundaryArgs& b, float* U, float* R, const float* L1,
@@ -786,7 +821,80 @@ cudaError_t launch_mode(const StepArgs& a, const BoundaryArgs& b, float* U, floa
   }
 }
 
+template <bool XPASS, int PREC, int MM, bool SCAT_TC>
+cudaError_t launch_batched_one(const BatchProblem* probs, const BatchProblem* dev, int n, int step, int hl,
+                               cudaStream_t s) {
+  using K = Kind<PREC>;
+  size_t smem = 0;
+  int ctas = 0;
+  for (int p = 0; p < n; ++p) {
+    const TcLayout L(XPASS ? probs[p].a.nx : probs[p].a.ny, K::X3, K::KC);
+    const size_t body = static_cast<size_t>(L.stage_bytes) + kPBytes;
+    const size_t need = 1024 + (XPASS ? body : (body > kEpiBytes ? body : kEpiBytes));
+    if (need > smem) smem = need;
+    ctas += (XPASS ? probs[p].tiles_x : probs[p].tiles_y) * probs[p].a.G;
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc_pass_batched<XPASS, PREC, MM, SCAT_TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         232448 - 2048);
+    attr = true;
+  }
+  tc_pass_batched<XPASS, PREC, MM, SCAT_TC><<<ctas, kThreads, smem, s>>>(dev, n, step, hl);
+  return cudaGetLastError();
+}
+
+template <bool XPASS, int PREC>
+cudaError_t launch_batched_pass(const BatchProblem* probs, const BatchProblem* dev, int n, int step, int hl,
+                                cudaStream_t s) {
+  constexpr bool kScatOk = XPASS && !Kind<PREC>::BF;
+  const bool st = kScatOk && probs[0].a.tc_scatter != 0;
+  const int M = probs[0].a.M;
+  if (M == 16)
+    return st ? launch_batched_one<XPASS, PREC, 16, kScatOk>(probs, dev, n, step, hl, s)
+              : launch_batched_one<XPASS, PREC, 16, false>(probs, dev, n, step, hl, s);
+  if (M == 32)
+    return st ? launch_batched_one<XPASS, PREC, 32, kScatOk>(probs, dev, n, step, hl, s)
+              : launch_batched_one<XPASS, PREC, 32, false>(probs, dev, n, step, hl, s);
+  return launch_batched_one<XPASS, PREC, 64, false>(probs, dev, n, step, hl, s);
+}
+
+template <bool XPASS>
+cudaError_t launch_batched_mode(const BatchProblem* probs, const BatchProblem* dev, int n, int step, int hl,
+                                cudaStream_t s) {
+  switch (probs[0].a.tc_mode) {
+    case 1: return launch_batched_pass<XPASS, 1>(probs, dev, n, step, hl, s);
+    case 2: return launch_batched_pass<XPASS, 2>(probs, dev, n, step, hl, s);
+    case 3: return launch_batched_pass<XPASS, 3>(probs, dev, n, step, hl, s);
+    default: return launch_batched_pass<XPASS, 4>(probs, dev, n, step, hl, s);
+  }
+}
+
 }  // namespace
+
+void tc_batch_layout(BatchProblem* probs, int n, int* ctas_x, int* ctas_y) {
+  int cx = 0, cy = 0;
+  for (int p = 0; p < n; ++p) {
+    const int per_tile = kNC / probs[p].a.M;
+    probs[p].tiles_x = (probs[p].a.ny + per_tile - 1) / per_tile;
+    probs[p].tiles_y = (probs[p].a.nx + per_tile - 1) / per_tile;
+    probs[p].tile0_x = cx;
+    probs[p].tile0_y = cy;
+    cx += probs[p].tiles_x * probs[p].a.G;
+    cy += probs[p].tiles_y * probs[p].a.G;
+  }
+  *ctas_x = cx;
+  *ctas_y = cy;
+}
+
+cudaError_t launch_step_tc_batched(const BatchProblem* probs, const BatchProblem* probs_dev, int n, int step,
+                                   int hl, cudaStream_t s, long long* launches) {
+  cudaError_t e = launch_batched_mode<true>(probs, probs_dev, n, step, hl, s);
+  if (e != cudaSuccess) return e;
+  e = launch_batched_mode<false>(probs, probs_dev, n, step, hl, s);
+  if (launches) *launches += 2;
+  return e;
+}
 
 bool tc_supported(int nx, int ny, int M, int precision, int flags) {
   if (nx < 16 || ny < 16 || nx > 512 || ny > 512) return false;

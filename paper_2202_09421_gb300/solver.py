@@ -67,6 +67,9 @@ class FCDOMSolver:
     def kernel_launches(self) -> int:
         return B.rte_kernel_launches(self.ctx)
 
+    def graph_captures(self) -> int:
+        return B.rte_graph_captures(self.ctx)
+
     def close(self):
         if self.ctx is not None:
             B.rte_destroy(self.ctx)
@@ -77,6 +80,16 @@ class FCDOMSolver:
             self.close()
         except Exception:
             pass
+
+
+def forward_batch(solvers, groups_per_solver, n_steps: int):
+    """Advances several solvers (media of their own grid sizes, same M,
+    precision, flags and stream) through one forward march in lockstep
+    (rte_forward_batch); afterwards readout/objective/adjoint_gradient apply
+    per solver."""
+    B.rte_forward_batch([s.ctx for s in solvers], groups_per_solver, n_steps)
+    for s, groups in zip(solvers, groups_per_solver):
+        s.n_groups, s.n_steps = len(groups), n_steps
 
 
 class RTEObjective(torch.autograd.Function):
