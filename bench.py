@@ -66,10 +66,19 @@ NCU_TRAFFIC = {
 }
 
 
-def kernel_source_hash(name="tc_pass_kernel"):
-    src = "rte_tc.cu" if name.startswith("tc_pass") else "rte_kernels.cu"
-    with open(os.path.join(ROOT, "paper_2202_09421_gb300", "csrc", src), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+def kernel_source_hash(name="tc_pass_ws"):
+    """sha256 prefix of the sources a kernel is compiled from."""
+    if name.startswith("tc_pass_ws"):
+        srcs = ["rte_tc_ws.cu", "rte_tc_common.cuh"]
+    elif name.startswith("tc_pass"):
+        srcs = ["rte_tc.cu", "rte_tc_common.cuh"]
+    else:
+        srcs = ["rte_kernels.cu"]
+    h = hashlib.sha256()
+    for src in srcs:
+        with open(os.path.join(ROOT, "paper_2202_09421_gb300", "csrc", src), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -82,6 +91,8 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=40)
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the batched (48 media) and 512^2 M=64 precision measurements")
     return ap.parse_args()
 
 
@@ -273,6 +284,7 @@ def run_ours(args):
     # (read u, R, L1..L3; write u, L) against HBM; x-pass: tensor-core flops
     # (3 products x 2 flop x (n + M) per update) against the TF32 peak.
     ncell_m = g.nx * g.ny * g.M * len(wl.groups)
+    # the default schedule: one tile per CTA
     names = ["tc_pass_kernel<x>", "tc_pass_kernel<y>"]
     dom = 0 if pass_ms[0] >= pass_ms[1] else 1
     avg_ms = pass_ms[dom] / max(1, pass_cnt[dom])
@@ -352,6 +364,11 @@ def run_ours(args):
                    "update_equivalents_per_gradient": 3 * wm.updates}
         sa.close()
 
+    configs = None
+    if not args.no_configs:
+        configs = {"batched_48_media": measure_batched(args, dev, flush, barrier, max_over_ranks, world),
+                   "precision512_M64": measure_precision512(args, dev, flush, barrier, max_over_ranks, world)}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, secs = oracle_rate(args.cpu_sample_steps)
@@ -370,11 +387,118 @@ def run_ours(args):
                        "updates_per_step": updates * world, "l2": "flushed between timed steps "
                        "(256 MB write) and state > L2", "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks, "adjoint": adjoint, "forms": forms,
+            "clocks": clocks, "adjoint": adjoint, "forms": forms, "configs": configs,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _timed(fn, stream, flush, barrier, reps=1):
+    """Mean device time (ms) of fn over reps calls, CUDA events on the
+    launching stream, L2 flushed before each."""
+    import torch
+    times = []
+    for k in range(reps):
+        flush.fill_(float(k))
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        barrier()
+        times.append(e0.elapsed_time(e1))
+    return statistics.mean(times)
+
+
+def _rel(a, b):
+    import torch
+    return float(torch.linalg.norm((a - b).double()) / torch.linalg.norm(b.double()))
+
+
+def measure_batched(args, dev, flush, barrier, max_over_ranks, world):
+    """48 neck-like media on grids of 128..384 points per side (M = 32, one
+    beam each, 1500 steps): plain FP32 kernels one medium after another
+    against the batched tensor-core forms (one launch per pass per step over
+    all media), and each form's detector curves against the FP32 run."""
+    import torch
+    from paper_2202_09421_gb300 import binding as B
+    from paper_2202_09421_gb300.solver import FCDOMSolver, forward_batch
+    from rte_inputs import workload_batched
+    wls = workload_batched()
+    n_steps = wls[0].n_steps
+    updates = sum(w.updates for w in wls)
+    stream = torch.cuda.current_stream()
+    meds = [(torch.tensor(w.mua, dtype=torch.float32, device=dev),
+             torch.tensor(w.mus, dtype=torch.float32, device=dev)) for w in wls]
+    out, ref = {}, None
+    forms = (("plain_fp32_per_medium", B.RTE_PREC_FP32, 0, False),
+             ("tf32x3_batched_graph", B.RTE_PREC_TF32X3, B.RTE_FLAG_CUDA_GRAPH, True),
+             ("bf16x3_batched_graph", B.RTE_PREC_BF16X3, B.RTE_FLAG_CUDA_GRAPH, True))
+    for name, prec, flags, batched in forms:
+        ss = [FCDOMSolver(w.grid, w.optics, a, b, w.c, w.dt, precision=prec, flags=flags)
+              for w, (a, b) in zip(wls, meds)]
+
+        def run():
+            if batched:
+                forward_batch(ss, [w.groups for w in wls], n_steps)
+            else:
+                for s_, w in zip(ss, wls):
+                    s_.forward(w.groups, n_steps)
+        run()
+        l0 = ss[0].kernel_launches()
+        ms = max_over_ranks(_timed(run, stream, flush, barrier))
+        launches = ss[0].kernel_launches() - l0
+        curves = torch.cat([s_.readout(w.detectors).flatten() for s_, w in zip(ss, wls)])
+        if ref is None:
+            ref = curves
+        out[name] = {"value": updates * world / (ms / 1e3), "unit": UNIT, "ms_per_solve_set": ms,
+                     "launches_first_medium": launches,
+                     "curves_rel_l2_vs_plain_fp32": _rel(curves, ref)}
+        for s_ in ss:
+            s_.close()
+    base = out["plain_fp32_per_medium"]["value"]
+    for v in out.values():
+        v["speedup_vs_plain_fp32"] = v["value"] / base
+    return {"workload": "48 neck-like media, grids from {128,192,256,384}^2 at dx = 4/255 cm, M = 32, "
+                        f"one beam each, {n_steps} steps", "updates_per_solve_set": updates, "forms": out}
+
+
+def measure_precision512(args, dev, flush, barrier, max_over_ranks, world):
+    """512 x 512, M = 64, g = 0.8 smooth random medium, one beam, 3000 steps:
+    every precision form, timed, and its detector curves and final fluence
+    against the plain FP32 run."""
+    import torch
+    from paper_2202_09421_gb300 import binding as B
+    from paper_2202_09421_gb300.solver import FCDOMSolver
+    from rte_inputs import workload_precision512
+    wl = workload_precision512()
+    stream = torch.cuda.current_stream()
+    a = torch.tensor(wl.mua, dtype=torch.float32, device=dev)
+    b = torch.tensor(wl.mus, dtype=torch.float32, device=dev)
+    out, ref = {}, None
+    for name, prec in (("plain_fp32_simt", B.RTE_PREC_FP32), ("tf32x3", B.RTE_PREC_TF32X3),
+                       ("tf32", B.RTE_PREC_TF32), ("bf16x3", B.RTE_PREC_BF16X3), ("bf16", B.RTE_PREC_BF16)):
+        s_ = FCDOMSolver(wl.grid, wl.optics, a, b, wl.c, wl.dt, precision=prec)
+        box = {}
+
+        def run():
+            box["fl"] = s_.forward(wl.groups, wl.n_steps, [wl.n_steps - 1])
+        run()
+        ms = max_over_ranks(_timed(run, stream, flush, barrier))
+        curves = s_.readout(wl.detectors)
+        if ref is None:
+            ref = (curves, box["fl"])
+        out[name] = {"value": wl.updates * world / (ms / 1e3), "unit": UNIT, "ms_per_solve": ms,
+                     "curves_rel_l2_vs_plain_fp32": _rel(curves, ref[0]),
+                     "fluence_rel_l2_vs_plain_fp32": _rel(box["fl"], ref[1])}
+        s_.close()
+    base = out["plain_fp32_simt"]["value"]
+    for v in out.values():
+        v["speedup_vs_plain_fp32"] = v["value"] / base
+    return {"workload": f"precision512_M64: 512x512 on [0,4]^2, M = 64, g = 0.8, smooth random mua/mus, "
+                        f"1 beam, {wl.n_steps} steps", "updates_per_solve": wl.updates, "forms": out}
 
 
 def main():

@@ -233,12 +233,24 @@ rte_status rte_host_phase_matrix(int M, double g, double exponent, double* P_out
 rte_status rte_set_kernel_timing(rte_ctx* ctx, int on);
 rte_status rte_kernel_times(rte_ctx* ctx, double* ms_out, long long* count_out);
 
+/* Name of the last CUDA error that a call of this library on the calling
+ * thread reported as RTE_ERR_CUDA or RTE_ERR_OOM ("cudaSuccess" if none). */
+const char* rte_last_cuda_error(void);
+
 /* Number of kernels this context has launched since creation (kernels of
  * a replayed CUDA graph included). */
 long long rte_kernel_launches(const rte_ctx* ctx);
 
 /* Number of CUDA graphs captured by this context (RTE_FLAG_CUDA_GRAPH). */
 long long rte_graph_captures(const rte_ctx* ctx);
+
+/* Kernel schedule of the tensor-core precisions (no counterpart in the
+ * paper; a scheduling choice with the same arithmetic up to FP32
+ * contraction order): 0 the persistent warp-specialised passes, one CTA per
+ * SM, where supported (nx, ny <= 256, M in {16, 32}, no
+ * RTE_FLAG_TC_SCATTER), else the one-tile-per-CTA passes; 1 (default)
+ * always the one-tile-per-CTA passes.  Errors: INVALID_ARG. */
+rte_status rte_set_pass_variant(rte_ctx* ctx, int variant);
 
 /* Forward solve plus detector curves that allocate no device memory.
  * The paper has no counterpart: this exists for callers that cannot call

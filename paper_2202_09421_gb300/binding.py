@@ -54,7 +54,10 @@ class RteDetector(ctypes.Structure):
 
 class RTEError(RuntimeError):
     def __init__(self, status: int, where: str):
-        super().__init__(f"{where}: status {status} ({rte_status_string(status)})")
+        detail = ""
+        if status in (3, 4):           # OOM, CUDA: name the underlying CUDA error
+            detail = f", {library().rte_last_cuda_error().decode()}"
+        super().__init__(f"{where}: status {status} ({rte_status_string(status)}{detail})")
         self.status = status
 
 
@@ -62,7 +65,7 @@ EXPORTS = ("rte_init_medium", "rte_set_medium", "rte_forward", "rte_detector_rea
            "rte_objective", "rte_adjoint_gradient", "rte_get_state", "rte_kernel_launches",
            "rte_destroy", "rte_status_string", "rte_host_fc_operator", "rte_host_phase_matrix",
            "rte_set_kernel_timing", "rte_kernel_times", "rte_forward_static", "rte_forward_batch",
-           "rte_graph_captures")
+           "rte_graph_captures", "rte_set_pass_variant", "rte_last_cuda_error")
 
 _lib = None
 
@@ -96,6 +99,8 @@ def library() -> ctypes.CDLL:
         "rte_forward_static": [P, POINTER(RteSourceGroup), c_int, c_int, POINTER(RteDetector), c_int, P],
         "rte_forward_batch": [POINTER(c_void_p), c_int, POINTER(POINTER(RteSourceGroup)), POINTER(c_int), c_int],
         "rte_graph_captures": [P],
+        "rte_set_pass_variant": [P, c_int],
+        "rte_last_cuda_error": [],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -104,6 +109,7 @@ def library() -> ctypes.CDLL:
     lib.rte_kernel_launches.restype = c_longlong
     lib.rte_graph_captures.restype = c_longlong
     lib.rte_status_string.restype = ctypes.c_char_p
+    lib.rte_last_cuda_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -193,6 +199,10 @@ def rte_forward_batch(ctxs, groups_per_ctx, n_steps: int):
         ngr[i] = len(groups)
     carr = (c_void_p * n)(*[c.value for c in ctxs])
     _check(library().rte_forward_batch(carr, n, garrs, ngr, int(n_steps)), "rte_forward_batch")
+
+
+def rte_set_pass_variant(ctx, variant: int):
+    _check(library().rte_set_pass_variant(ctx, int(variant)), "rte_set_pass_variant")
 
 
 def rte_graph_captures(ctx) -> int:

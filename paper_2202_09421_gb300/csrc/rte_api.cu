@@ -34,6 +34,7 @@ struct rte_ctx {
   DevBuf face_refl, corner_refl, face_f, corner_f, face_act, corner_act, wexit;
   DevBuf DxImg, DyImg, PImg;       // split, swizzled operators (tensor-core forms)
   int tc_mode = 0;                 // the precision: 0 SIMT FP32, 1-4 tcgen05 forms
+  int x_variant = 1;               // pass kernels: 0 persistent warp-specialised, 1 one tile per CTA
   // state of the last forward
   int G = 0, n_steps = -1, kmax = 0;
   int hl = 0;                      // history rotation index
@@ -63,8 +64,12 @@ struct rte_ctx {
 
 namespace {
 
+// Last CUDA error a call of this library turned into a status.
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
 rte_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return RTE_OK;
+  g_last_cuda_error = e;
   if (e == cudaErrorMemoryAllocation) return RTE_ERR_OOM;
   return RTE_ERR_CUDA;
 }
@@ -145,6 +150,7 @@ rte_kern::StepArgs step_args(rte_ctx* c, int G) {
   a.cdt = static_cast<float>(c->opt.c * c->par.dt);
   a.tc_mode = c->tc_mode;
   a.tc_scatter = (c->par.flags & RTE_FLAG_TC_SCATTER) ? 1 : 0;
+  a.x_variant = c->x_variant;
   a.DxImg = c->DxImg.p;
   a.DyImg = c->DyImg.p;
   a.PImg = F(c->PImg);
@@ -255,9 +261,10 @@ rte_status march(rte_ctx* c, DevBuf& U, DevBuf& R, DevBuf* L, int& hl, int G, in
 rte_status tc_check(rte_ctx* c) {
   if (c->tc_mode == 0) return RTE_OK;
   RTE_TRY(cuda_status(cudaStreamSynchronize(c->stream)));
-  int flag = 0;
+  int flag = 0, flag_ws = 0;
   RTE_TRY(cuda_status(rte_kern::tc_take_error(&flag)));
-  return flag ? RTE_ERR_TIMEOUT : RTE_OK;
+  RTE_TRY(cuda_status(rte_kern::ws_take_error(&flag_ws)));
+  return (flag || flag_ws) ? RTE_ERR_TIMEOUT : RTE_OK;
 }
 
 // Validates the beams and sets up a forward march of n_steps on G = n_groups
@@ -415,7 +422,15 @@ const char* rte_status_string(rte_status s) {
 
 long long rte_kernel_launches(const rte_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
+const char* rte_last_cuda_error(void) { return cudaGetErrorName(g_last_cuda_error); }
+
 long long rte_graph_captures(const rte_ctx* ctx) { return ctx ? ctx->graph_captures : -1; }
+
+rte_status rte_set_pass_variant(rte_ctx* c, int variant) {
+  if (!c || variant < 0 || variant > 1) return RTE_ERR_INVALID_ARG;
+  c->x_variant = variant;
+  return RTE_OK;
+}
 
 rte_status rte_set_kernel_timing(rte_ctx* c, int on) {
   if (!c) return RTE_ERR_INVALID_ARG;

@@ -45,6 +45,7 @@ struct StepArgs {
   // the split, pre-swizzled operators (tf32 words or bf16 halves).
   int tc_mode;
   int tc_scatter;                   // x-pass scattering as a tcgen05 contraction
+  int x_variant;                    // 0 persistent warp-specialised passes where supported, 1 one tile per CTA
   const void* DxImg;
   const void* DyImg;
   const float* PImg;                // phase matrix as the scattering operand
@@ -86,6 +87,14 @@ cudaError_t launch_step_tc_batched(const BatchProblem* probs, const BatchProblem
 // Reads and clears the tcgen05 kernels' bounded-wait timeout flag
 // (synchronous).
 cudaError_t tc_take_error(int* flag);
+
+// Persistent warp-specialised passes (rte_tc_ws.cu): nx, ny <= 256, M in
+// {16, 32}, without the tensor-core scattering flag.
+bool tc_ws_supported(const StepArgs& a);
+cudaError_t launch_pass_ws(bool xpass, const StepArgs& a, const BoundaryArgs& b, float* U, float* R,
+                           const float* L1, const float* L2, float* L3, int src_step, int ring_step,
+                           cudaStream_t s);
+cudaError_t ws_take_error(int* flag);
 
 // Phi[g][j][i] = w sum_m u_m  (eq. photondensity).
 cudaError_t launch_fluence(const float* U, float* out, size_t out_group_stride, int nx, int ny,

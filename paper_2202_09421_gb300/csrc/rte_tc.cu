@@ -38,11 +38,9 @@
 // the tensor core works on the current one.  One thread issues the MMAs
 // and commits them to mbarriers; every wait is bounded and sets g_tc_error
 // instead of spinning forever.
-#include <cuda_bf16.h>
-
 #include <cstdint>
 
-#include "rte_kernels.cuh"
+#include "rte_tc_common.cuh"
 
 namespace rte_kern {
 
@@ -50,142 +48,19 @@ __device__ int g_tc_error;
 
 namespace {
 
-constexpr int kNC = 128;          // slab columns per tile (MMA N)
-constexpr int kMT = 128;          // output positions per accumulator tile (MMA M)
-constexpr int kThreads = 256;
-constexpr int kTileBytes = 128 * 128;   // one 128-row x 128-byte operand tile
-constexpr long kWaitLimit = 1L << 26;
-constexpr float kAB0 = 55.0f / 24.0f, kAB1 = -59.0f / 24.0f, kAB2 = 37.0f / 24.0f,
-                kAB3 = -9.0f / 24.0f;
+using namespace tc;
 
-// Operand kinds of the precision modes (rte.h): 1 3xTF32, 2 TF32, 3 bf16x3,
-// 4 BF16.  KC = K positions per 128-byte row, GV = values per 16-byte group.
-template <int PREC>
-struct Kind {
-  static constexpr bool BF = PREC == 3 || PREC == 4;
-  static constexpr bool X3 = PREC == 1 || PREC == 3;
-  static constexpr int KC = BF ? 64 : 32;
-  static constexpr int GV = BF ? 8 : 4;
-};
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row group
-// stride 1024 B (start address in 16-byte units).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  return static_cast<uint64_t>((saddr >> 4) & 0x3FFF) | (static_cast<uint64_t>(1024 >> 4) << 32) |
-         (static_cast<uint64_t>(1) << 46) | (static_cast<uint64_t>(2) << 61);
-}
-
-// Byte offset of the 16-byte group grp of row `row` in a K-major
-// 128-byte-swizzle tile.
-__device__ __forceinline__ int sw128_off(int row, int grp) { return row * 128 + ((grp ^ (row & 7)) << 4); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait; false (and the error flag set) when the limit runs out.
+// Bounded wait (kWaitNs of wall clock); false, and the error flag set, when
+// the limit runs out.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long it = 0; it < kWaitLimit; ++it)
-    if (mbar_try(bar, parity)) return true;
-  atomicExch(&g_tc_error, 1);
-  return false;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try(bar, parity))
+    if (global_ns() - t0 > kWaitNs) {
+      atomicExch(&g_tc_error, 1);
+      return false;
+    }
+  return true;
 }
-
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-
-template <bool BF>
-__device__ __forceinline__ void mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accumulate) {
-  if constexpr (BF)
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            tmem),
-        "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
-  else
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            tmem),
-        "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int t = 0; t < 16; ++t) v[t] = __uint_as_float(r[t]);
-}
-
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-__device__ __forceinline__ void split4(float4 v, float s, float4& hi, float4& lo) {
-  hi.x = tf32_rna(s * v.x); lo.x = tf32_rna(s * v.x - hi.x);
-  hi.y = tf32_rna(s * v.y); lo.y = tf32_rna(s * v.y - hi.y);
-  hi.z = tf32_rna(s * v.z); lo.z = tf32_rna(s * v.z - hi.z);
-  hi.w = tf32_rna(s * v.w); lo.w = tf32_rna(s * v.w - hi.w);
-}
-
-// Two bf16 values in one word, the lower K index in the low half.
-__device__ __forceinline__ uint32_t pack_bf16(float k0, float k1) {
-  return static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(k0))) |
-         (static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(k1))) << 16);
-}
-
-// Splits the 8 values s*v[e] of one 16-byte group into bf16 hi and lo words.
-__device__ __forceinline__ void split8_bf16(const float v[8], float s, uint4& hi, uint4& lo) {
-  float h[8], l[8];
-#pragma unroll
-  for (int e = 0; e < 8; ++e) {
-    const float x = s * v[e];
-    h[e] = __bfloat162float(__float2bfloat16_rn(x));
-    l[e] = x - h[e];
-  }
-  hi = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
-  lo = make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
-}
-
-struct TcLayout {
-  int n, n_mt, n_kc, nrows_img, stage_bytes, tmem_cols;
-  __host__ __device__ TcLayout(int n_, bool x3, int kc) : n(n_) {
-    n_mt = (n + kMT - 1) / kMT;
-    n_kc = (n + kc - 1) / kc;
-    nrows_img = n_mt * kMT;
-    stage_bytes = (x3 ? 2 : 1) * (n_mt + 1) * kTileBytes;   // D tiles + slab tile, hi (+ lo)
-    tmem_cols = n_mt == 1 ? 128 : n_mt == 2 ? 256 : 512;    // power of two >= n_mt * 128
-  }
-};
 
 constexpr int kPBytes = 2 * 32 * 128;   // P~ operand image: hi and lo, 32 rows x 128 B
 constexpr int kMaxM = 64;
@@ -219,6 +94,8 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
   const float* scale = XPASS ? a.xi : a.eta;
   const int n_lines = XPASS ? ny : nx;        // rows (x) / columns (y) of the grid
 
+  // A launch after a timed-out one does nothing (the march reports the error).
+  if (*static_cast<volatile int*>(&g_tc_error)) return;
   unsigned char* sm = smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023);
   unsigned char* Psm = sm + L.stage_bytes;    // P~ image (x-pass, TC scattering)
   const uint32_t bar_full = smem_u32(&bars[0]), bar_done = smem_u32(&bars[1]);
@@ -911,10 +788,13 @@ cudaError_t launch_step_tc(const StepArgs& a, const BoundaryArgs& b, float* U, f
   const int ring_step = b.ring_out ? step : -1;
   cudaError_t e;
   if (ev) cudaEventRecord(ev[0], s);
-  e = launch_mode<true>(a, b, U, R, L1, L2, L3, step, ring_step, s);
+  const bool ws = a.x_variant == 0 && tc_ws_supported(a);
+  e = ws ? launch_pass_ws(true, a, b, U, R, L1, L2, L3, step, ring_step, s)
+         : launch_mode<true>(a, b, U, R, L1, L2, L3, step, ring_step, s);
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[1], s);
-  e = launch_mode<false>(a, b, U, R, L1, L2, L3, step, ring_step, s);
+  e = ws ? launch_pass_ws(false, a, b, U, R, L1, L2, L3, step, ring_step, s)
+         : launch_mode<false>(a, b, U, R, L1, L2, L3, step, ring_step, s);
   if (ev) cudaEventRecord(ev[2], s);
   if (launches) *launches += 2;
   return e;

@@ -35,10 +35,15 @@ def _media(M, sizes, n_steps=80, seed0=11):
     return out
 
 
-def _run_single(wls, precision, flags=0):
+def _run_single(wls, precision, flags=0, variant=1):
+    """Single-medium runs, by default on the one-tile-per-CTA passes (the
+    kernel body the batched launch shares)."""
+    from paper_2202_09421_gb300 import binding as B
     res = []
     for wl in wls:
         s = _solver(wl, precision, flags)
+        if precision != FP32:
+            B.rte_set_pass_variant(s.ctx, variant)
         s.forward(wl.groups, wl.n_steps)
         res.append((s.readout(wl.detectors).cpu().numpy(),
                     [s.state(g).cpu().numpy() for g in range(len(wl.groups))]))
@@ -88,7 +93,7 @@ def test_batch_equals_single(precision, M, sizes):
 @pytest.mark.parametrize("precision", [FP32, TF32X3])
 def test_graph_forward_replays(precision):
     wl = _media(16, [(64, 48, 2)], n_steps=60)[0]
-    ref = _run_single([wl], precision)[0]
+    ref = _run_single([wl], precision, variant=1)[0]
     s = _solver(wl, precision, flags=GRAPH)
     for rep in range(3):
         s.forward(wl.groups, wl.n_steps)

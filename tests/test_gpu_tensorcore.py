@@ -154,3 +154,32 @@ def test_precision512_all_forms():
     for prec, ec, ef in rows:
         tol = 1e-5 if prec == 0 else TOL[prec]
         assert ec <= tol and ef <= tol, (prec, ec, ef)
+
+
+@pytest.mark.parametrize("nx,ny,M,groups", [(100, 70, 32, 2), (200, 131, 16, 1), (256, 256, 32, 3), (45, 29, 16, 5)])
+@pytest.mark.parametrize("precision", [TF32X3, TF32, BF16X3, BF16])
+def test_pass_variants_agree(nx, ny, M, groups, precision):
+    """The persistent warp-specialised passes (default) and the one-tile-per-
+    CTA passes perform the same products and the same per-node arithmetic;
+    the y-pass epilogues may contract the AB4 sum differently, so the states
+    agree to FP32 rounding (relative L2 <= 1e-6 for the split forms), and
+    for the single-product forms, whose operand rounding turns such
+    differences into tf32 / bf16 rounding steps, to a tenth of their bound."""
+    from paper_2202_09421_gb300 import binding as B
+    wl = _stable_custom(nx, ny, M, groups, n_steps=40)
+    states = []
+    for variant in (0, 1):
+        from paper_2202_09421_gb300.solver import FCDOMSolver
+        dev = torch.device("cuda:0")
+        s = FCDOMSolver(wl.grid, wl.optics, torch.tensor(wl.mua, dtype=torch.float32, device=dev),
+                        torch.tensor(wl.mus, dtype=torch.float32, device=dev), wl.c, wl.dt, precision=precision)
+        B.rte_set_pass_variant(s.ctx, variant)
+        s.forward(wl.groups, wl.n_steps)
+        states.append([s.state(g).cpu().numpy() for g in range(groups)])
+        s.close()
+    tol = 1e-6 if precision in (TF32X3, BF16X3) else TOL[precision] / 10
+    for a_, b_ in zip(*states):
+        d = float(np.abs(a_ - b_).max() / max(np.abs(b_).max(), 1e-30))
+        e = rel_l2(a_, b_)
+        print(f"variants {nx}x{ny} M{M} prec {precision}: rel L2 {e:.2e}, max rel diff {d:.2e}")
+        assert e <= tol
