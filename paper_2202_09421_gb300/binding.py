@@ -65,7 +65,8 @@ EXPORTS = ("rte_init_medium", "rte_set_medium", "rte_forward", "rte_detector_rea
            "rte_objective", "rte_adjoint_gradient", "rte_get_state", "rte_kernel_launches",
            "rte_destroy", "rte_status_string", "rte_host_fc_operator", "rte_host_phase_matrix",
            "rte_set_kernel_timing", "rte_kernel_times", "rte_forward_static", "rte_forward_batch",
-           "rte_graph_captures", "rte_set_pass_variant", "rte_last_cuda_error")
+           "rte_graph_captures", "rte_set_pass_variant", "rte_last_cuda_error",
+           "rte_autotune")
 
 _lib = None
 
@@ -101,6 +102,7 @@ def library() -> ctypes.CDLL:
         "rte_graph_captures": [P],
         "rte_set_pass_variant": [P, c_int],
         "rte_last_cuda_error": [],
+        "rte_autotune": [P, POINTER(RteSourceGroup), c_int, c_int, POINTER(c_int), POINTER(ctypes.c_float)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -203,6 +205,19 @@ def rte_forward_batch(ctxs, groups_per_ctx, n_steps: int):
 
 def rte_set_pass_variant(ctx, variant: int):
     _check(library().rte_set_pass_variant(ctx, int(variant)), "rte_set_pass_variant")
+
+
+def rte_autotune(ctx, groups, n_trial_steps: int):
+    """Returns (choice, {choice: ms}) of the configurations tried."""
+    beam_arrays = [make_beams(bl) for bl in groups]
+    garr = (RteSourceGroup * len(groups))()
+    for k, bl in enumerate(groups):
+        garr[k] = RteSourceGroup(ctypes.cast(beam_arrays[k], POINTER(RteBeam)), len(bl))
+    choice = c_int()
+    ms = (ctypes.c_float * 4)(-1.0, -1.0, -1.0, -1.0)
+    _check(library().rte_autotune(ctx, garr, len(groups), int(n_trial_steps), ctypes.byref(choice), ms),
+           "rte_autotune")
+    return choice.value, {k: ms[k] for k in range(4) if ms[k] >= 0.0}
 
 
 def rte_graph_captures(ctx) -> int:

@@ -267,6 +267,18 @@ rte_status tc_check(rte_ctx* c) {
   return (flag || flag_ws) ? RTE_ERR_TIMEOUT : RTE_OK;
 }
 
+// Split, swizzled phase matrix for the tensor-core scattering contraction
+// (built once, when the form is first used).
+rte_status ensure_phase_image(rte_ctx* c) {
+  if (c->PImg.p) return RTE_OK;
+  std::vector<double> P;
+  rte_setup::phase_matrix(c->M, c->opt.g, c->opt.hg_exponent, P);
+  std::vector<float> img;
+  rte_setup::tc_phase_image(P, c->M, img);
+  RTE_TRY(upload(c->PImg, img, c->stream));
+  return cuda_status(cudaStreamSynchronize(c->stream));   // img must outlive the copy
+}
+
 // Validates the beams and sets up a forward march of n_steps on G = n_groups
 // groups: state buffers, checkpoint store, source factors, zero state.
 rte_status prepare_forward(rte_ctx* c, const rte_source_group* groups, int n_groups, int n_steps) {
@@ -397,6 +409,8 @@ void append_forward_key(const rte_ctx* c, std::vector<unsigned long long>& key) 
   key.push_back(static_cast<unsigned long long>(c->n_steps));
   key.push_back(static_cast<unsigned long long>(c->G));
   key.push_back(static_cast<unsigned long long>(c->kmax));
+  key.push_back(static_cast<unsigned long long>(c->x_variant));
+  key.push_back(static_cast<unsigned long long>(c->par.flags));
   for (const void* p : ptrs) key.push_back(key_ptr(p));
 }
 
@@ -429,6 +443,63 @@ long long rte_graph_captures(const rte_ctx* ctx) { return ctx ? ctx->graph_captu
 rte_status rte_set_pass_variant(rte_ctx* c, int variant) {
   if (!c || variant < 0 || variant > 1) return RTE_ERR_INVALID_ARG;
   c->x_variant = variant;
+  return RTE_OK;
+}
+
+rte_status rte_autotune(rte_ctx* c, const rte_source_group* groups, int n_groups, int n_trial_steps,
+                        int* choice_out, float* ms_out) {
+  if (!c || !groups || n_groups <= 0 || n_trial_steps < 4 || !choice_out) return RTE_ERR_INVALID_ARG;
+  *choice_out = (c->x_variant & 1) | ((c->par.flags & RTE_FLAG_TC_SCATTER) ? 2 : 0);
+  if (c->tc_mode == 0) return RTE_OK;                     // one kernel family, nothing to choose
+  rte_kern::StepArgs probe = step_args(c, n_groups);
+  std::vector<int> cands;
+  for (int choice = 0; choice < 4; ++choice) {
+    const int variant = choice & 1;
+    const bool scat = (choice & 2) != 0;
+    if (scat && !rte_kern::tc_supported(c->nx, c->ny, c->M, c->tc_mode, RTE_FLAG_TC_SCATTER)) continue;
+    probe.x_variant = variant;
+    probe.tc_scatter = scat ? 1 : 0;
+    if (variant == 0 && !rte_kern::tc_ws_supported(probe)) continue;   // would run the other schedule
+    cands.push_back(choice);
+  }
+  const int keep_variant = c->x_variant, keep_flags = c->par.flags;
+  const bool keep_timing = c->timing;
+  c->timing = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  rte_status st = cuda_status(cudaEventCreate(&e0));
+  if (st == RTE_OK) st = cuda_status(cudaEventCreate(&e1));
+  float best = 0.f;
+  int best_choice = -1;
+  for (size_t k = 0; k < cands.size() && st == RTE_OK; ++k) {
+    const int choice = cands[k];
+    c->x_variant = choice & 1;
+    c->par.flags = (keep_flags & ~RTE_FLAG_TC_SCATTER) | ((choice & 2) ? RTE_FLAG_TC_SCATTER : 0);
+    if (choice & 2) st = ensure_phase_image(c);
+    // one untimed forward, then a timed one
+    if (st == RTE_OK) st = rte_forward(c, groups, n_groups, n_trial_steps, nullptr, 0, nullptr);
+    if (st == RTE_OK) st = cuda_status(cudaEventRecord(e0, c->stream));
+    if (st == RTE_OK) st = rte_forward(c, groups, n_groups, n_trial_steps, nullptr, 0, nullptr);
+    if (st == RTE_OK) st = cuda_status(cudaEventRecord(e1, c->stream));
+    if (st == RTE_OK) st = cuda_status(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    if (st == RTE_OK) st = cuda_status(cudaEventElapsedTime(&ms, e0, e1));
+    if (st == RTE_OK && ms_out) ms_out[choice] = ms;
+    if (st == RTE_OK && (best_choice < 0 || ms < best)) {
+      best = ms;
+      best_choice = choice;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  c->timing = keep_timing;
+  if (st != RTE_OK || best_choice < 0) {
+    c->x_variant = keep_variant;
+    c->par.flags = keep_flags;
+    return st != RTE_OK ? st : RTE_ERR_STATE;
+  }
+  c->x_variant = best_choice & 1;
+  c->par.flags = (keep_flags & ~RTE_FLAG_TC_SCATTER) | ((best_choice & 2) ? RTE_FLAG_TC_SCATTER : 0);
+  *choice_out = best_choice;
   return RTE_OK;
 }
 
@@ -590,11 +661,7 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
       area[static_cast<size_t>(j) * g->nx + i] = static_cast<float>(wx * wy);
     }
   rte_status s = RTE_OK;
-  std::vector<float> Pimg;
-  if (c->tc_mode != 0 && (p->flags & RTE_FLAG_TC_SCATTER)) {
-    rte_setup::tc_phase_image(P, g->M, Pimg);
-    s = upload(c->PImg, Pimg, c->stream);
-  }
+  if (c->tc_mode != 0 && (p->flags & RTE_FLAG_TC_SCATTER)) s = ensure_phase_image(c);
   if (s == RTE_OK) s = upload(c->PT, PTf, c->stream);
   if (s == RTE_OK) s = upload(c->xi, xi, c->stream);
   if (s == RTE_OK) s = upload(c->eta, eta, c->stream);

@@ -70,6 +70,11 @@ class FCDOMSolver:
     def graph_captures(self) -> int:
         return B.rte_graph_captures(self.ctx)
 
+    def autotune(self, groups, n_trial_steps: int = 40):
+        """Times the kernel configurations of this precision on these groups
+        and keeps the fastest; returns (choice, {choice: ms})."""
+        return B.rte_autotune(self.ctx, groups, n_trial_steps)
+
     def close(self):
         if self.ctx is not None:
             B.rte_destroy(self.ctx)

@@ -183,3 +183,26 @@ def test_pass_variants_agree(nx, ny, M, groups, precision):
         e = rel_l2(a_, b_)
         print(f"variants {nx}x{ny} M{M} prec {precision}: rel L2 {e:.2e}, max rel diff {d:.2e}")
         assert e <= tol
+
+
+@pytest.mark.parametrize("precision", [TF32X3, BF16X3])
+def test_autotune_keeps_a_valid_configuration(precision):
+    """rte_autotune times the admissible configurations and keeps the fastest;
+    the forward it leaves behind still meets the precision's parity bound."""
+    from paper_2202_09421_gb300.solver import FCDOMSolver
+    wl = _stable_custom(100, 70, 32, 2)
+    dev = torch.device("cuda:0")
+    s = FCDOMSolver(wl.grid, wl.optics, torch.tensor(wl.mua, dtype=torch.float32, device=dev),
+                    torch.tensor(wl.mus, dtype=torch.float32, device=dev), wl.c, wl.dt, precision=precision)
+    choice, ms = s.autotune(wl.groups, 12)
+    print(f"autotune prec {precision}: choice {choice}, times {ms}")
+    assert choice in ms and ms[choice] == min(ms.values())
+    expected = {0, 1, 3} if precision == TF32X3 else {0, 1}    # the persistent schedule has no TC scattering
+    assert set(ms) == expected
+    s.forward(wl.groups, wl.n_steps)
+    curves = s.readout(wl.detectors).cpu().numpy()
+    s.close()
+    c_ref, _, _ = oracle_forward(wl, snaps=[])
+    e = rel_l2(curves, c_ref)
+    print(f"autotune prec {precision}: curves rel L2 {e:.2e}")
+    assert e <= TOL[precision]
