@@ -60,9 +60,14 @@ NCU_TRAFFIC = {
     # profiles/fcdom_passes_tomo256_ncu_full.md
     ("xpass_kernel", "7ec20f8a420c3adc"): 136.062464e6 + 86.956800e6,
     ("ypass_kernel", "7ec20f8a420c3adc"): 672.236800e6 + 234.185472e6,
-    # tcgen05 3xTF32 passes (csrc/rte_tc.cu): profiles/tc_passes_tomo256_ncu_full.md
-    ("tc_pass_kernel<x>", "a1462982e931f755"): 136.674304e6 + 84.280320e6,
-    ("tc_pass_kernel<y>", "a1462982e931f755"): 751.340032e6 + 234.558208e6,
+    # tcgen05 3xTF32 passes, one tile per CTA (csrc/rte_tc.cu + rte_tc_common.cuh):
+    # profiles/tc_passes_tomo256_ncu_full.md
+    ("tc_pass_kernel<x>", "d42913758fb9a244"): 136.596992e6 + 83.779584e6,
+    ("tc_pass_kernel<y>", "d42913758fb9a244"): 751.724800e6 + 234.193920e6,
+    # persistent warp-specialised passes (csrc/rte_tc_ws.cu + rte_tc_common.cuh):
+    # profiles/tc_pass_ws_tomo256_ncu_full.md
+    ("tc_pass_ws<x>", "ff308bb1883a1817"): 135.533568e6 + 83.505152e6,
+    ("tc_pass_ws<y>", "ff308bb1883a1817"): 794.347520e6 + 235.415040e6,
 }
 
 
@@ -91,6 +96,10 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=40)
+    ap.add_argument("--schedule", default="auto", choices=["auto", "one-tile", "persistent"],
+                    help="tensor-core pass schedule: autotuned, one tile per CTA (the default "
+                         "configuration), or persistent warp-specialised")
+    ap.add_argument("--no-autotune", action="store_true", help="same as --schedule one-tile")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the batched (48 media) and 512^2 M=64 precision measurements")
     return ap.parse_args()
@@ -246,7 +255,15 @@ def run_ours(args):
         """Forward solve + detector readout per step; CUDA events on the
         launching stream; L2 flushed before every timed step."""
         solver = FCDOMSolver(g, wl.optics, a, b, wl.c, wl.dt, ckpt_interval=0, precision=precision)
-        tuned = solver.autotune(wl.groups, 40) if precision != B.RTE_PREC_FP32 else (None, {})
+        schedule = "one-tile" if args.no_autotune else args.schedule
+        if precision == B.RTE_PREC_FP32:
+            tuned = (1, {})
+        elif schedule == "auto":
+            tuned = solver.autotune(wl.groups, 40)
+        else:
+            variant = 0 if schedule == "persistent" else 1
+            B.rte_set_pass_variant(solver.ctx, variant)
+            tuned = (variant, {})
 
         def one_step():
             solver.forward(wl.groups, wl.n_steps, [wl.n_steps - 1])
