@@ -60,6 +60,9 @@ struct rte_ctx {
   std::vector<unsigned long long> gkey;
   long long glaunches = 0;         // kernels per replay
   long long graph_captures = 0;
+  // adjoint pipeline: segment recompute on a second stream
+  cudaStream_t astream = nullptr;
+  cudaEvent_t aev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -564,6 +567,12 @@ rte_status rte_destroy(rte_ctx* c) {
     cudaStreamSynchronize(c->gstream);
     cudaStreamDestroy(c->gstream);
   }
+  for (cudaEvent_t e : c->aev)
+    if (e) cudaEventDestroy(e);
+  if (c->astream) {
+    cudaStreamSynchronize(c->astream);
+    cudaStreamDestroy(c->astream);
+  }
   delete c;
   return RTE_OK;
 }
@@ -865,7 +874,11 @@ rte_status rte_adjoint_gradient(rte_ctx* c, const rte_detector* dets, int n_det,
   RTE_TRY(ensure(c->MU, gbytes));
   RTE_TRY(ensure(c->RA, gbytes));
   for (int q = 0; q < 3; ++q) RTE_TRY(ensure(c->LA[q], gbytes));
-  RTE_TRY(ensure(c->seg, static_cast<size_t>(I) * gbytes));
+  RTE_TRY(ensure(c->seg, 2 * static_cast<size_t>(I) * gbytes));   // two segment buffers
+  if (!c->astream) {
+    RTE_TRY(cuda_status(cudaStreamCreateWithFlags(&c->astream, cudaStreamNonBlocking)));
+    for (int k = 0; k < 4; ++k) RTE_TRY(cuda_status(cudaEventCreateWithFlags(&c->aev[k], cudaEventDisableTiming)));
+  }
   const int* lo = static_cast<const int*>(c->lohi.p);
 
   // Detector curves (FP64), residual and objective (eq. FObj), then the
@@ -891,20 +904,59 @@ rte_status rte_adjoint_gradient(rte_ctx* c, const rte_detector* dets, int n_det,
   std::vector<int> no_snaps(N, -1);
   // Levels needed: forward steps 0 .. N-2 (the adjoint vanishes at the last).
   const int last = N - 2;
-  for (int seg = c->n_ckpt - 1; seg >= 0; --seg) {
-    const int s0 = seg * I;
-    const int s_end = std::min(s0 + I, last + 1);
-    if (s0 > last) continue;
+  // Segments in reverse order.  The forward recompute of a segment (second
+  // stream, into segment buffer b = k % 2) overlaps the adjoint march of the
+  // segment before it in this order (context stream, reading the other
+  // buffer).  Events: done_fwd[b] (recompute into b finished) orders the
+  // adjoint after it; done_adj[b] (adjoint that read b finished) orders the
+  // next recompute into b after it.
+  std::vector<int> segs;
+  for (int seg = c->n_ckpt - 1; seg >= 0; --seg)
+    if (seg * I <= last) segs.push_back(seg);
+  cudaEvent_t* done_fwd = c->aev;
+  cudaEvent_t* done_adj = c->aev + 2;
+  // the recompute stream starts after everything queued so far
+  RTE_TRY(cuda_status(cudaEventRecord(done_adj[0], c->stream)));
+  RTE_TRY(cuda_status(cudaStreamWaitEvent(c->astream, done_adj[0], 0)));
+  auto seg_ptrs = [&](int k, int s0, int s_end) {
+    std::vector<float*> segp(s_end - s0);
+    const size_t base = static_cast<size_t>(k % 2) * I * gfloats;
+    for (int q = 0; q < s_end - s0; ++q) segp[q] = F(c->seg) + base + static_cast<size_t>(q) * gfloats;
+    return segp;
+  };
+  auto recompute = [&](int k) -> rte_status {
+    const int seg = segs[k];
+    const int s0 = seg * I, s_end = std::min(s0 + I, last + 1);
+    const cudaStream_t keep = c->stream;
+    c->stream = c->astream;
+    const bool keep_timing = c->timing;
+    c->timing = false;
     // Restore the AB4 state of the checkpoint and recompute the segment.
     const char* base = static_cast<const char*>(c->ckpt.p) + static_cast<size_t>(seg) * 4 * gbytes;
-    RTE_TRY(cuda_status(cudaMemcpyAsync(c->U.p, base, gbytes, cudaMemcpyDeviceToDevice, c->stream)));
-    for (int q = 0; q < 3; ++q)
-      RTE_TRY(cuda_status(cudaMemcpyAsync(c->L[q].p, base + (q + 1) * gbytes, gbytes,
-                                          cudaMemcpyDeviceToDevice, c->stream)));
+    rte_status st = cuda_status(cudaMemcpyAsync(c->U.p, base, gbytes, cudaMemcpyDeviceToDevice, c->stream));
+    for (int q = 0; q < 3 && st == RTE_OK; ++q)
+      st = cuda_status(cudaMemcpyAsync(c->L[q].p, base + (q + 1) * gbytes, gbytes, cudaMemcpyDeviceToDevice,
+                                       c->stream));
     int hl = 0;
-    std::vector<float*> segp(s_end - s0);
-    for (int k = 0; k < s_end - s0; ++k) segp[k] = F(c->seg) + static_cast<size_t>(k) * gfloats;
-    RTE_TRY(march(c, c->U, c->R, c->L, hl, G, s0, s_end, bf, false, no_snaps, nullptr, &segp));
+    std::vector<float*> segp = seg_ptrs(k, s0, s_end);
+    if (st == RTE_OK) st = march(c, c->U, c->R, c->L, hl, G, s0, s_end, bf, false, no_snaps, nullptr, &segp);
+    if (st == RTE_OK) st = cuda_status(cudaEventRecord(done_fwd[k % 2], c->stream));
+    c->stream = keep;
+    c->timing = keep_timing;
+    return st;
+  };
+  if (!segs.empty()) RTE_TRY(recompute(0));
+  for (size_t k = 0; k < segs.size(); ++k) {
+    const int seg = segs[k];
+    const int s0 = seg * I, s_end = std::min(s0 + I, last + 1);
+    // next segment's recompute may start once the adjoint that read its
+    // buffer (segment k - 1) is done
+    if (k + 1 < segs.size()) {
+      if (k >= 1) RTE_TRY(cuda_status(cudaStreamWaitEvent(c->astream, done_adj[(k + 1) % 2], 0)));
+      RTE_TRY(recompute(static_cast<int>(k + 1)));
+    }
+    RTE_TRY(cuda_status(cudaStreamWaitEvent(c->stream, done_fwd[k % 2], 0)));
+    std::vector<float*> segp = seg_ptrs(static_cast<int>(k), s0, s_end);
     // Adjoint steps for levels s_end-1 .. s0 (eq. AdjointProblem, flipped).
     for (int lvl = s_end - 1; lvl >= s0; --lvl) {
       float* L1 = F(c->LA[hl_adj]);
@@ -919,6 +971,7 @@ rte_status rte_adjoint_gradient(rte_ctx* c, const rte_detector* dets, int n_det,
                                                 dJ_dmus ? D(c->grad_b) : nullptr, c->stream,
                                                 &c->launches)));
     }
+    RTE_TRY(cuda_status(cudaEventRecord(done_adj[k % 2], c->stream)));
   }
   // The forward state buffers now hold a recomputed state; mark them stale.
   if (dJ_dmua)
