@@ -100,6 +100,9 @@ def parse():
                     help="tensor-core pass schedule: autotuned, one tile per CTA (the default "
                          "configuration), or persistent warp-specialised")
     ap.add_argument("--no-autotune", action="store_true", help="same as --schedule one-tile")
+    ap.add_argument("--inverse", type=int, default=0, metavar="ITERS",
+                    help="also run the inverse solver (Algorithm 2) for ITERS L-BFGS-B iterations, "
+                         "single sources against staggered groups")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the batched (48 media) and 512^2 M=64 precision measurements")
     return ap.parse_args()
@@ -389,6 +392,8 @@ def run_ours(args):
         configs = {"batched_48_media": measure_batched(args, dev, flush, barrier, max_over_ranks, world),
                    "precision512_M64": measure_precision512(args, dev, flush, barrier, max_over_ranks, world)}
 
+    inverse = measure_inverse(dev, args.inverse) if args.inverse > 0 else None
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, secs = oracle_rate(args.cpu_sample_steps)
@@ -410,7 +415,7 @@ def run_ours(args):
                        "updates_per_step": updates * world, "l2": "flushed between timed steps "
                        "(256 MB write) and state > L2", "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks, "adjoint": adjoint, "forms": forms, "configs": configs,
+            "clocks": clocks, "adjoint": adjoint, "forms": forms, "configs": configs, "inverse": inverse,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -522,6 +527,47 @@ def measure_precision512(args, dev, flush, barrier, max_over_ranks, world):
         v["speedup_vs_plain_fp32"] = v["value"] / base
     return {"workload": f"precision512_M64: 512x512 on [0,4]^2, M = 64, g = 0.8, smooth random mua/mus, "
                         f"1 beam, {wl.n_steps} steps", "updates_per_solve": wl.updates, "forms": out}
+
+
+def measure_inverse(dev, iters):
+    """Algorithm 2 on the 64 x 64, M = 32 inverse workload (a 1 cm square,
+    two absorbing disks in a known background, 2000 steps): data from the
+    target medium
+    plus 10 % seeded noise, L-BFGS-B on the absorption within [0.1, 1]
+    /cm from the background, with the 16 beams as single sources (TS) and
+    as 4 staggered groups (MSS).  Reports E(i), J and the wall time."""
+    import torch
+    from paper_2202_09421_gb300 import binding as B
+    from paper_2202_09421_gb300.inverse import gpu_evaluator, node_areas, reconstruct
+    from paper_2202_09421_gb300.solver import FCDOMSolver
+    from rte_inputs import add_relative_noise, workload_inverse
+    out = {}
+    for mode in ("ts", "mss"):
+        wl, tgt = workload_inverse(mode), workload_inverse(mode, target=True)
+        mus = torch.tensor(wl.mus, dtype=torch.float32, device=dev)
+        st = FCDOMSolver(tgt.grid, tgt.optics, torch.tensor(tgt.mua, dtype=torch.float32, device=dev), mus,
+                         tgt.c, tgt.dt, precision=B.RTE_PREC_TF32X3)
+        st.forward(tgt.groups, tgt.n_steps)
+        clean = st.readout(tgt.detectors).cpu().numpy()
+        st.close()
+        meas = torch.tensor(add_relative_noise(clean, 0.10), dtype=torch.float32, device=dev)
+        solver = FCDOMSolver(wl.grid, wl.optics, torch.tensor(wl.mua, dtype=torch.float32, device=dev), mus,
+                             wl.c, wl.dt, ckpt_interval=100, precision=B.RTE_PREC_TF32X3)
+        ev = gpu_evaluator(solver, wl.groups, wl.n_steps, wl.detectors, meas, mus)
+        res = reconstruct(ev, wl.mua, 0.1, 1.0, max_iter=iters, a_true=tgt.mua, area=node_areas(wl.grid))
+        solver.close()
+        hist = res["history"]
+        secs = hist[-1]["seconds"]
+        out[mode] = {"groups": len(wl.groups), "iterations": len(hist) - 1, "objective_evaluations": res["nfev"],
+                     "seconds": secs, "seconds_per_evaluation": secs / max(1, res["nfev"]),
+                     "E": [h["E"] for h in hist], "J": [h["J"] for h in hist],
+                     "seconds_at_iteration": [h["seconds"] for h in hist]}
+    out["workload"] = ("inverse64: 64x64 on a 1 cm square, M = 32, background mua 0.1 / mus 100, two seeded "
+                       "absorbing disks, 16 beams (TS: 16 sources; MSS: 4 staggered groups), 32 detectors, "
+                       "2000 steps at dt 0.04 ps, 10 % noise, bounds [0.1, 1] /cm, 3xTF32, checkpoint every 100")
+    out["mss_speedup_per_evaluation"] = (out["ts"]["seconds_per_evaluation"] /
+                                         out["mss"]["seconds_per_evaluation"])
+    return out
 
 
 def main():

@@ -5,9 +5,9 @@ from here, so that each side computes everything else on its own."""
 from .workloads import (Beam, Detector, Grid, Optics, Workload, face_point,
                         perimeter_detectors, workload_small, workload_tomo256,
                         workload_precision512, workload_mss256, workload_batched,
-                        workload_custom)
+                        workload_custom, workload_inverse, add_relative_noise)
 
 __all__ = ["Beam", "Detector", "Grid", "Optics", "Workload", "face_point",
            "perimeter_detectors", "workload_small", "workload_tomo256",
            "workload_precision512", "workload_mss256", "workload_batched",
-           "workload_custom"]
+           "workload_custom", "workload_inverse", "add_relative_noise"]

@@ -336,3 +336,48 @@ def workload_custom(nx: int, ny: int, M: int, n_steps: int, dt: float,
     return Workload(f"custom{nx}x{ny}_M{M}", grid, Optics(g=g), a, b,
                     C0_CM_PER_PS / 1.4, dt, n_steps, groups, dets,
                     snap_steps=[n_steps - 1])
+
+
+def add_relative_noise(curves: np.ndarray, level: float = 0.10, seed: int = BASE_SEED + 7) -> np.ndarray:
+    """Synthetic measurement noise: every detector reading G becomes
+    G (1 + level xi) with xi ~ N(0, 1) drawn from a seeded generator (the
+    reading taken of the paper's "10% random noise")."""
+    rng = np.random.default_rng(seed)
+    return curves * (1.0 + level * rng.standard_normal(curves.shape))
+
+
+def workload_inverse(mode: str = "mss", n: int = 64, n_steps: int = 2000, dt: float = 0.04,
+                     target: bool = False, seed: int = BASE_SEED + 8) -> Workload:
+    """Inverse-problem medium: n x n points at dx = 2/127 cm (n = 64: a 1 cm
+    square, which the diffusing light crosses within the 80 ps window),
+    M = 32, background mua = 0.1 (the lower bound of the reconstruction),
+    mus = 100, g = 0.9; the target adds two seeded absorbing disks (mua
+    0.3-0.6, r 0.15-0.3 * L/2 cm).  mode "ts": 16 single-beam sources, 4 per
+    face; "mss": the same 16 beams as 4 staggered groups (one per face,
+    delays in [0, T/2]); 32 detectors, 8 per face."""
+    rng = np.random.default_rng(seed)
+    h = 2.0 / 127
+    L = h * (n - 1)
+    grid = Grid(n, n, 0.0, L, 0.0, L, 32)
+    a = np.full((n, n), 0.1)
+    b = np.full((n, n), 100.0)
+    X, Y = _coords(grid)
+    disks = []
+    for _ in range(2):
+        r = rng.uniform(0.15, 0.3) * L / 2
+        cx, cy = rng.uniform(0.3 * L, 0.7 * L), rng.uniform(0.3 * L, 0.7 * L)
+        disks.append((cx, cy, r, rng.uniform(0.3, 0.6)))
+    if target:
+        for cx, cy, r, av in disks:
+            a[(X - cx) ** 2 + (Y - cy) ** 2 <= r * r] = av
+    T = n_steps * dt
+    beams = []
+    for gi in range(4):
+        grp = []
+        for face in FACES:
+            x, y, th = face_point(face, (gi + 0.5) / 4, L)
+            grp.append(Beam(x, y, th, tau=float(rng.uniform(0, T / 2)) if mode == "mss" else 0.0))
+        beams.append(grp)
+    groups = beams if mode == "mss" else [[bm] for grp in beams for bm in grp]
+    return Workload(f"inverse{n}_{mode}", grid, Optics(g=0.9), a, b, C0_CM_PER_PS / 1.4, dt, n_steps,
+                    groups, perimeter_detectors(L, 8))
