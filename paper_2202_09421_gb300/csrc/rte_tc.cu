@@ -62,6 +62,29 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return true;
 }
 
+// L2 eviction priorities (createpolicy): the slab values are read again by
+// the epilogue of the same CTA, the epilogue's other streams only once.
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void st_hint(float* ptr, float4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(ptr), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ float ld_hint(const float* ptr, uint64_t pol) {
+  float v;
+  asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(ptr), "l"(pol));
+  return v;
+}
+
 constexpr int kPBytes = 2 * 32 * 128;   // P~ operand image: hi and lo, 32 rows x 128 B
 constexpr int kMaxM = 64;
 // y-pass epilogue: two 5-array buffers, three [16][128] tiles, boundary tables
@@ -135,6 +158,7 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
   // this chunk's MMAs so that their latency overlaps the tensor core.
   constexpr int kItems = kNC * (KC / GV) / kThreads;   // 4
   float v[kItems][GV];
+  const uint64_t pol_keep = policy_evict_last();
   auto load_chunk = [&](int q) {
     const int k0 = q * KC;
 #pragma unroll
@@ -151,7 +175,7 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
         if (valid && k < n) {
           const size_t idx = XPASS ? goff + (static_cast<size_t>(line) * nx + k) * M + m
                                    : goff + (static_cast<size_t>(k) * nx + line) * M + m;
-          v[t][e] = U[idx];
+          v[t][e] = ld_hint(U + idx, pol_keep);
         }
       }
     }
@@ -425,7 +449,9 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
               acc[m] = fmaf(bcur, sc, acc[m] - abcur * uu[m]);
             }
 #pragma unroll
-            for (int k = 0; k < MM / 4; ++k) rp[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+            for (int k = 0; k < MM / 4; ++k)
+              st_hint(reinterpret_cast<float*>(rp + k), make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]),
+                      pol_keep);   // R is read by the y-pass that follows
           }
         }
         if (SCAT_TC) {
@@ -472,6 +498,7 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
       bc_act[e] = face ? b.face_act[k] : b.corner_act[k];
       if (face) bc_wexit[e] = b.wexit[k];
     }
+    const uint64_t pol_once = policy_evict_first();
     auto issue_chunk = [&](int cc, int bsel) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -483,7 +510,8 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
 #pragma unroll
         for (int arr = 0; arr < kEpiArr; ++arr) {
           float* dst = ebuf + bsel * kBufFloats + (arr * 16 + t) * kNC + c;
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(srcs[arr] + gidx)
+          asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)),
+                       "l"(srcs[arr] + gidx), "l"(pol_once)
                        : "memory");
         }
       }
@@ -533,7 +561,7 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
           *reinterpret_cast<float4*>(L3 + gidx) = lk;
           const bool bnd = i == 0 || i == nx - 1 || j == 0 || j == ny - 1;
           if (chunk_bnd) *reinterpret_cast<float4*>(un_s + t * kNC + c) = un;
-          if (!bnd) *reinterpret_cast<float4*>(U + gidx) = un;
+          if (!bnd) st_hint(U + gidx, un, pol_keep);   // u^{k+1} is read by the next x-pass
         }
       }
       if (chunk_bnd) {
