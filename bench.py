@@ -62,8 +62,8 @@ NCU_TRAFFIC = {
     ("ypass_kernel", "7ec20f8a420c3adc"): 672.236800e6 + 234.185472e6,
     # tcgen05 3xTF32 passes, one tile per CTA (csrc/rte_tc.cu + rte_tc_common.cuh):
     # profiles/tc_passes_tomo256_ncu_full.md
-    ("tc_pass_kernel<x>", "d42913758fb9a244"): 136.596992e6 + 83.779584e6,
-    ("tc_pass_kernel<y>", "d42913758fb9a244"): 751.724800e6 + 234.193920e6,
+    ("tc_pass_kernel<x>", "08e5d86e3171048e"): 136.694272e6 + 83.250688e6,
+    ("tc_pass_kernel<y>", "08e5d86e3171048e"): 686.802432e6 + 192.235264e6,
     # persistent warp-specialised passes (csrc/rte_tc_ws.cu + rte_tc_common.cuh):
     # profiles/tc_pass_ws_tomo256_ncu_full.md
     ("tc_pass_ws<x>", "ff308bb1883a1817"): 135.533568e6 + 83.505152e6,
