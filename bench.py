@@ -75,6 +75,8 @@ def kernel_source_hash(name="tc_pass_ws"):
     """sha256 prefix of the sources a kernel is compiled from."""
     if name.startswith("tc_pass_ws"):
         srcs = ["rte_tc_ws.cu", "rte_tc_common.cuh"]
+    elif name.startswith("tc_ypass_pipe"):
+        srcs = ["rte_tc_pipe.cu", "rte_tc_common.cuh"]
     elif name.startswith("tc_pass"):
         srcs = ["rte_tc.cu", "rte_tc_common.cuh"]
     else:
@@ -96,9 +98,10 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=40)
-    ap.add_argument("--schedule", default="auto", choices=["auto", "one-tile", "persistent"],
+    ap.add_argument("--schedule", default="auto", choices=["auto", "one-tile", "persistent", "pipelined"],
                     help="tensor-core pass schedule: autotuned, one tile per CTA (the default "
-                         "configuration), or persistent warp-specialised")
+                         "configuration), persistent warp-specialised, or one-tile x-pass with the "
+                         "pipelined persistent y-pass")
     ap.add_argument("--no-autotune", action="store_true", help="same as --schedule one-tile")
     ap.add_argument("--inverse", type=int, default=0, metavar="ITERS",
                     help="also run the inverse solver (Algorithm 2) for ITERS L-BFGS-B iterations, "
@@ -264,7 +267,7 @@ def run_ours(args):
         elif schedule == "auto":
             tuned = solver.autotune(wl.groups, 40)
         else:
-            variant = 0 if schedule == "persistent" else 1
+            variant = {"persistent": 0, "one-tile": 1, "pipelined": 2}[schedule]
             B.rte_set_pass_variant(solver.ctx, variant)
             tuned = (variant, {})
 
@@ -305,10 +308,12 @@ def run_ours(args):
     # (read u, R, L1..L3; write u, L) against HBM; x-pass: tensor-core flops
     # (3 products x 2 flop x (n + M) per update) against the TF32 peak.
     ncell_m = g.nx * g.ny * g.M * len(wl.groups)
-    # the autotuned configuration: bit 0 the schedule (0 persistent
-    # warp-specialised, 1 one tile per CTA), bit 1 tensor-core scattering
-    kern = "tc_pass_ws" if (tuned[0] & 1) == 0 else "tc_pass_kernel"
-    names = [kern + "<x>", kern + "<y>"]
+    # the configuration timed: schedule = choice % 3 (0 persistent
+    # warp-specialised, 1 one tile per CTA, 2 pipelined y-pass), choice >= 3
+    # tensor-core scattering
+    sched = tuned[0] % 3
+    names = {0: ["tc_pass_ws<x>", "tc_pass_ws<y>"], 1: ["tc_pass_kernel<x>", "tc_pass_kernel<y>"],
+             2: ["tc_pass_kernel<x>", "tc_ypass_pipe<y>"]}[sched]
     dom = 0 if pass_ms[0] >= pass_ms[1] else 1
     avg_ms = pass_ms[dom] / max(1, pass_cnt[dom])
     if dom == 1:
@@ -410,8 +415,8 @@ def run_ours(args):
             "config": {"workload": WORKLOAD_DESC,
                        "form": "tcgen05 tensor cores, split 3xTF32 operands (FP32-level accuracy)",
                        "autotune": {"choice": tuned[0], "trial_ms_per_40_steps": tuned[1],
-                                    "choices": "bit 0: 0 persistent warp-specialised / 1 one tile per CTA; "
-                                               "bit 1: tensor-core scattering"},
+                                    "choices": "choice % 3: 0 persistent warp-specialised, 1 one tile per "
+                                               "CTA, 2 pipelined y-pass; choice >= 3: tensor-core scattering"},
                        "updates_per_step": updates * world, "l2": "flushed between timed steps "
                        "(256 MB write) and state > L2", "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

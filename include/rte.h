@@ -246,25 +246,29 @@ long long rte_graph_captures(const rte_ctx* ctx);
 
 /* Kernel schedule of the tensor-core precisions (no counterpart in the
  * paper; a scheduling choice with the same arithmetic up to FP32
- * contraction order): 0 the persistent warp-specialised passes, one CTA per
- * SM, where supported (nx, ny <= 256, M in {16, 32}, no
- * RTE_FLAG_TC_SCATTER), else the one-tile-per-CTA passes; 1 (default)
- * always the one-tile-per-CTA passes.  Errors: INVALID_ARG. */
+ * contraction order):
+ *   0  persistent warp-specialised x- and y-passes, one CTA per SM, where
+ *      supported (nx, ny <= 256, M in {16, 32}, no RTE_FLAG_TC_SCATTER);
+ *   1  (default) one-tile-per-CTA passes;
+ *   2  one-tile-per-CTA x-pass and the pipelined persistent y-pass (the main
+ *      loop of one tile and the epilogue of the previous one on two warp
+ *      groups of one CTA per SM) where supported (ny <= 256).
+ * Unsupported sizes run the one-tile-per-CTA passes.  Errors: INVALID_ARG. */
 rte_status rte_set_pass_variant(rte_ctx* ctx, int variant);
 
 /* Autotuner (no counterpart in the paper): times every kernel configuration
  * the context's precision admits, with CUDA events around one forward of
  * n_trial_steps (>= 4) of the given groups after an untimed one, and keeps
- * the fastest in the context.  A configuration is choice = variant |
- * (2 if the x-pass scattering is the tensor-core contraction): bit 0 the
- * schedule of rte_set_pass_variant (0 persistent, 1 one tile per CTA),
- * bit 1 RTE_FLAG_TC_SCATTER.  Configurations a size does not support are
- * skipped; all of them meet the precision's parity bound.  *choice_out
- * receives the chosen configuration, ms_out (host, 4 entries, may be NULL)
- * the time of each configuration tried (untouched entries for the others).
- * The trial forwards replace the context's last-forward results.  In
- * RTE_PREC_FP32 there is one configuration and nothing is run.
- * Errors: INVALID_ARG, the errors of rte_forward. */
+ * the fastest in the context.  A configuration is choice = schedule +
+ * 3 * (1 if the x-pass scattering is the tensor-core contraction), with the
+ * schedule of rte_set_pass_variant (0, 1, 2) and RTE_FLAG_TC_SCATTER.
+ * Configurations a size does not support are skipped; all of them meet the
+ * precision's parity bound.  *choice_out receives the chosen configuration,
+ * ms_out (host, 6 entries, may be NULL) the time of each configuration tried
+ * (entries of the others are untouched).  The trial forwards replace the
+ * context's last-forward results.  In RTE_PREC_FP32 there is one
+ * configuration and nothing is run.  Errors: INVALID_ARG, the errors of
+ * rte_forward. */
 rte_status rte_autotune(rte_ctx* ctx, const rte_source_group* groups, int n_groups,
                         int n_trial_steps, int* choice_out, float* ms_out);
 

@@ -34,7 +34,7 @@ struct rte_ctx {
   DevBuf face_refl, corner_refl, face_f, corner_f, face_act, corner_act, wexit;
   DevBuf DxImg, DyImg, PImg;       // split, swizzled operators (tensor-core forms)
   int tc_mode = 0;                 // the precision: 0 SIMT FP32, 1-4 tcgen05 forms
-  int x_variant = 1;               // pass kernels: 0 persistent warp-specialised, 1 one tile per CTA
+  int x_variant = 1;               // pass kernels: 0 persistent warp-specialised, 1 one tile per CTA, 2 pipelined y-pass
   // state of the last forward
   int G = 0, n_steps = -1, kmax = 0;
   int hl = 0;                      // history rotation index
@@ -264,10 +264,11 @@ rte_status march(rte_ctx* c, DevBuf& U, DevBuf& R, DevBuf* L, int& hl, int G, in
 rte_status tc_check(rte_ctx* c) {
   if (c->tc_mode == 0) return RTE_OK;
   RTE_TRY(cuda_status(cudaStreamSynchronize(c->stream)));
-  int flag = 0, flag_ws = 0;
+  int flag = 0, flag_ws = 0, flag_pipe = 0;
   RTE_TRY(cuda_status(rte_kern::tc_take_error(&flag)));
   RTE_TRY(cuda_status(rte_kern::ws_take_error(&flag_ws)));
-  return (flag || flag_ws) ? RTE_ERR_TIMEOUT : RTE_OK;
+  RTE_TRY(cuda_status(rte_kern::pipe_take_error(&flag_pipe)));
+  return (flag || flag_ws || flag_pipe) ? RTE_ERR_TIMEOUT : RTE_OK;
 }
 
 // Split, swizzled phase matrix for the tensor-core scattering contraction
@@ -444,7 +445,7 @@ const char* rte_last_cuda_error(void) { return cudaGetErrorName(g_last_cuda_erro
 long long rte_graph_captures(const rte_ctx* ctx) { return ctx ? ctx->graph_captures : -1; }
 
 rte_status rte_set_pass_variant(rte_ctx* c, int variant) {
-  if (!c || variant < 0 || variant > 1) return RTE_ERR_INVALID_ARG;
+  if (!c || variant < 0 || variant > 2) return RTE_ERR_INVALID_ARG;
   c->x_variant = variant;
   return RTE_OK;
 }
@@ -452,17 +453,19 @@ rte_status rte_set_pass_variant(rte_ctx* c, int variant) {
 rte_status rte_autotune(rte_ctx* c, const rte_source_group* groups, int n_groups, int n_trial_steps,
                         int* choice_out, float* ms_out) {
   if (!c || !groups || n_groups <= 0 || n_trial_steps < 4 || !choice_out) return RTE_ERR_INVALID_ARG;
-  *choice_out = (c->x_variant & 1) | ((c->par.flags & RTE_FLAG_TC_SCATTER) ? 2 : 0);
+  *choice_out = c->x_variant + ((c->par.flags & RTE_FLAG_TC_SCATTER) ? 3 : 0);
   if (c->tc_mode == 0) return RTE_OK;                     // one kernel family, nothing to choose
   rte_kern::StepArgs probe = step_args(c, n_groups);
   std::vector<int> cands;
-  for (int choice = 0; choice < 4; ++choice) {
-    const int variant = choice & 1;
-    const bool scat = (choice & 2) != 0;
+  for (int choice = 0; choice < 6; ++choice) {
+    const int variant = choice % 3;
+    const bool scat = choice >= 3;
     if (scat && !rte_kern::tc_supported(c->nx, c->ny, c->M, c->tc_mode, RTE_FLAG_TC_SCATTER)) continue;
     probe.x_variant = variant;
     probe.tc_scatter = scat ? 1 : 0;
-    if (variant == 0 && !rte_kern::tc_ws_supported(probe)) continue;   // would run the other schedule
+    // skip configurations that would fall back to another one
+    if (variant == 0 && !rte_kern::tc_ws_supported(probe)) continue;
+    if (variant == 2 && !rte_kern::tc_pipe_supported(probe)) continue;
     cands.push_back(choice);
   }
   const int keep_variant = c->x_variant, keep_flags = c->par.flags;
@@ -475,9 +478,9 @@ rte_status rte_autotune(rte_ctx* c, const rte_source_group* groups, int n_groups
   int best_choice = -1;
   for (size_t k = 0; k < cands.size() && st == RTE_OK; ++k) {
     const int choice = cands[k];
-    c->x_variant = choice & 1;
-    c->par.flags = (keep_flags & ~RTE_FLAG_TC_SCATTER) | ((choice & 2) ? RTE_FLAG_TC_SCATTER : 0);
-    if (choice & 2) st = ensure_phase_image(c);
+    c->x_variant = choice % 3;
+    c->par.flags = (keep_flags & ~RTE_FLAG_TC_SCATTER) | (choice >= 3 ? RTE_FLAG_TC_SCATTER : 0);
+    if (choice >= 3) st = ensure_phase_image(c);
     // one untimed forward, then a timed one
     if (st == RTE_OK) st = rte_forward(c, groups, n_groups, n_trial_steps, nullptr, 0, nullptr);
     if (st == RTE_OK) st = cuda_status(cudaEventRecord(e0, c->stream));
@@ -500,8 +503,8 @@ rte_status rte_autotune(rte_ctx* c, const rte_source_group* groups, int n_groups
     c->par.flags = keep_flags;
     return st != RTE_OK ? st : RTE_ERR_STATE;
   }
-  c->x_variant = best_choice & 1;
-  c->par.flags = (keep_flags & ~RTE_FLAG_TC_SCATTER) | ((best_choice & 2) ? RTE_FLAG_TC_SCATTER : 0);
+  c->x_variant = best_choice % 3;
+  c->par.flags = (keep_flags & ~RTE_FLAG_TC_SCATTER) | (best_choice >= 3 ? RTE_FLAG_TC_SCATTER : 0);
   *choice_out = best_choice;
   return RTE_OK;
 }

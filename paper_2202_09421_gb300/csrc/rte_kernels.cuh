@@ -45,7 +45,7 @@ struct StepArgs {
   // the split, pre-swizzled operators (tf32 words or bf16 halves).
   int tc_mode;
   int tc_scatter;                   // x-pass scattering as a tcgen05 contraction
-  int x_variant;                    // 0 persistent warp-specialised passes where supported, 1 one tile per CTA
+  int x_variant;                    // 0 persistent warp-specialised passes, 1 one tile per CTA, 2 pipelined y-pass
   const void* DxImg;
   const void* DyImg;
   const float* PImg;                // phase matrix as the scattering operand
@@ -95,6 +95,14 @@ cudaError_t launch_pass_ws(bool xpass, const StepArgs& a, const BoundaryArgs& b,
                            const float* L1, const float* L2, float* L3, int src_step, int ring_step,
                            cudaStream_t s);
 cudaError_t ws_take_error(int* flag);
+
+// Pipelined persistent y-pass (rte_tc_pipe.cu): ny <= 256, M in {16, 32, 64};
+// the main loop of one tile and the epilogue of the previous one run on two
+// warp groups of one CTA per SM.
+bool tc_pipe_supported(const StepArgs& a);
+cudaError_t launch_ypass_pipe(const StepArgs& a, const BoundaryArgs& b, float* U, const float* R, const float* L1,
+                              const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s);
+cudaError_t pipe_take_error(int* flag);
 
 // Phi[g][j][i] = w sum_m u_m  (eq. photondensity).
 cudaError_t launch_fluence(const float* U, float* out, size_t out_group_stride, int nx, int ny,

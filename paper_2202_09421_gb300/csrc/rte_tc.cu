@@ -62,29 +62,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return true;
 }
 
-// L2 eviction priorities (createpolicy): the slab values are read again by
-// the epilogue of the same CTA, the epilogue's other streams only once.
-__device__ __forceinline__ uint64_t policy_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t policy_evict_first() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ void st_hint(float* ptr, float4 v, uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(ptr), "f"(v.x), "f"(v.y),
-               "f"(v.z), "f"(v.w), "l"(pol)
-               : "memory");
-}
-__device__ __forceinline__ float ld_hint(const float* ptr, uint64_t pol) {
-  float v;
-  asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(ptr), "l"(pol));
-  return v;
-}
-
 constexpr int kPBytes = 2 * 32 * 128;   // P~ operand image: hi and lo, 32 rows x 128 B
 constexpr int kMaxM = 64;
 // y-pass epilogue: two 5-array buffers, three [16][128] tiles, boundary tables
@@ -817,12 +794,14 @@ cudaError_t launch_step_tc(const StepArgs& a, const BoundaryArgs& b, float* U, f
   cudaError_t e;
   if (ev) cudaEventRecord(ev[0], s);
   const bool ws = a.x_variant == 0 && tc_ws_supported(a);
+  const bool pipe = a.x_variant == 2 && tc_pipe_supported(a);
   e = ws ? launch_pass_ws(true, a, b, U, R, L1, L2, L3, step, ring_step, s)
          : launch_mode<true>(a, b, U, R, L1, L2, L3, step, ring_step, s);
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[1], s);
-  e = ws ? launch_pass_ws(false, a, b, U, R, L1, L2, L3, step, ring_step, s)
-         : launch_mode<false>(a, b, U, R, L1, L2, L3, step, ring_step, s);
+  e = ws     ? launch_pass_ws(false, a, b, U, R, L1, L2, L3, step, ring_step, s)
+      : pipe ? launch_ypass_pipe(a, b, U, R, L1, L2, L3, step, ring_step, s)
+             : launch_mode<false>(a, b, U, R, L1, L2, L3, step, ring_step, s);
   if (ev) cudaEventRecord(ev[2], s);
   if (launches) *launches += 2;
   return e;
