@@ -62,8 +62,8 @@ NCU_TRAFFIC = {
     ("ypass_kernel", "7ec20f8a420c3adc"): 672.236800e6 + 234.185472e6,
     # tcgen05 3xTF32 passes, one tile per CTA (csrc/rte_tc.cu + rte_tc_common.cuh):
     # profiles/tc_passes_tomo256_ncu_full.md
-    ("tc_pass_kernel<x>", "08e5d86e3171048e"): 136.694272e6 + 83.250688e6,
-    ("tc_pass_kernel<y>", "08e5d86e3171048e"): 686.802432e6 + 192.235264e6,
+    ("tc_pass_kernel<x>", "4f36e1185847c61d"): 136.543744e6 + 82.921984e6,
+    ("tc_pass_kernel<y>", "4f36e1185847c61d"): 687.281408e6 + 192.194304e6,
     # persistent warp-specialised passes (csrc/rte_tc_ws.cu + rte_tc_common.cuh):
     # profiles/tc_pass_ws_tomo256_ncu_full.md
     ("tc_pass_ws<x>", "ff308bb1883a1817"): 135.533568e6 + 83.505152e6,
