@@ -206,6 +206,42 @@ def fc_derivative(g: np.ndarray, h: float, axis: int = -1, tables=None,
     return np.moveaxis(dg.real[..., :n], -1, axis)
 
 
+FRINGE = 2   # fringe points added on each interior side of a subdomain (Sec. 4.4)
+
+
+def subdomain_segments(n: int, parts: int):
+    """The decomposition of Sec. 4.4 along one axis: the n points are split
+    into `parts` contiguous owned ranges [k n / parts, (k + 1) n / parts)
+    (the interior regions), and each owned range is extended by FRINGE
+    points on every side that is not a physical end of the line (the
+    overlapping subdomain).  Returns (lo, hi, seg_lo, seg_hi) per part."""
+    out = []
+    for k in range(parts):
+        lo, hi = k * n // parts, (k + 1) * n // parts
+        seg_lo = lo - FRINGE if k > 0 else lo
+        seg_hi = hi + FRINGE if k < parts - 1 else hi
+        out.append((lo, hi, seg_lo, seg_hi))
+    return out
+
+
+def fc_derivative_parts(g: np.ndarray, h: float, axis: int = -1, parts: int = 1, tables=None,
+                        alpha: float = FILTER_ALPHA, beta: float = FILTER_BETA) -> np.ndarray:
+    """The x- or y-derivative of the decomposed scheme of Algorithm 1: every
+    subdomain continues and differentiates its own segment (eq. RTEFCSumder
+    on that segment alone), and after the fringe exchange each point holds
+    the value its own subdomain computed, so a point's derivative is the
+    segment derivative of the part that owns it.  parts = 1 is the global
+    derivative."""
+    if parts <= 1:
+        return fc_derivative(g, h, axis=axis, tables=tables, alpha=alpha, beta=beta)
+    g = np.moveaxis(np.asarray(g, dtype=np.float64), axis, -1)
+    out = np.empty_like(g)
+    for lo, hi, slo, shi in subdomain_segments(g.shape[-1], parts):
+        d = fc_derivative(g[..., slo:shi], h, axis=-1, tables=tables, alpha=alpha, beta=beta)
+        out[..., lo:hi] = d[..., lo - slo:hi - slo]
+    return np.moveaxis(out, -1, axis)
+
+
 def derivative_matrix(n: int, h: float, tables=None) -> np.ndarray:
     """The dense n x n operator D with D @ g == fc_derivative(g, h): column j
     is the FC derivative of the j-th unit vector."""

@@ -198,12 +198,17 @@ def boundary_tables(grid, optics) -> BoundaryTables:
 
 
 # --------------------------------------------------------------------------
-# The solver: Algorithm 1 on one domain (no decomposition)
+# The solver: Algorithm 1, on one domain or decomposed (fc_parts)
 # --------------------------------------------------------------------------
 
 class Solver:
-    def __init__(self, wl, tables=None, fresnel_override=None):
+    """fc_parts = (parts along x, parts along y): the subdomain decomposition
+    of Sec. 4.4 / Algorithm 1 (FC on each part's segment with two fringe
+    points, fringes exchanged every step); (1, 1) is one domain."""
+
+    def __init__(self, wl, tables=None, fresnel_override=None, fc_parts=(1, 1)):
         self.wl = wl
+        self.fc_parts = tuple(fc_parts)
         g = wl.grid
         self.grid = g
         self.M = g.M
@@ -226,11 +231,11 @@ class Solver:
     # --- spatial operator ------------------------------------------------
     def dx(self, u):
         """Algorithm 1, x-lines: FC derivative along i for every (m, j)."""
-        return fcgram.fc_derivative(u, self.grid.dx, axis=2, tables=self.tables)
+        return fcgram.fc_derivative_parts(u, self.grid.dx, axis=2, parts=self.fc_parts[0], tables=self.tables)
 
     def dy(self, u):
         """Algorithm 1, y-lines: FC derivative along j for every (m, i)."""
-        return fcgram.fc_derivative(u, self.grid.dy, axis=1, tables=self.tables)
+        return fcgram.fc_derivative_parts(u, self.grid.dy, axis=1, parts=self.fc_parts[1], tables=self.tables)
 
     def scatter(self, u):
         """sum_{m'} w_{m'} p_{m,m'} u_{m'} at every node."""

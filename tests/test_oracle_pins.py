@@ -388,3 +388,53 @@ def test_photon_balance_with_fresnel_boundary():
         rhs = np.trapezoid(rate, dx=dt)
         errs.append(abs(lhs - rhs) / np.abs(N).max())
     assert max(errs) < 2e-3, errs
+
+
+# ---------------------------------------------------------------- subdomains
+def test_subdomain_segments_layout():
+    """Sec. 4.4: owned ranges tile the line, two fringe points on interior
+    sides only, neighbouring segments overlap by four points."""
+    from oracle.fcgram import subdomain_segments
+    segs = subdomain_segments(101, 4)
+    assert segs[0][0] == 0 and segs[-1][1] == 101
+    for (lo, hi, slo, shi), (lo2, hi2, slo2, shi2) in zip(segs, segs[1:]):
+        assert hi == lo2 and shi - slo2 == 4
+    assert segs[0][2] == 0 and segs[-1][3] == 101
+    assert all(slo == lo - 2 for lo, hi, slo, shi in segs[1:]) and all(shi == hi + 2 for lo, hi, slo, shi in segs[:-1])
+
+
+def test_subdomain_derivative_one_part_is_global():
+    from oracle.fcgram import fc_derivative, fc_derivative_parts
+    x = np.linspace(0.0, 2.0, 70)
+    g = np.stack([np.sin(3 * x), np.exp(-x) * x ** 2])
+    assert np.array_equal(fc_derivative_parts(g, x[1] - x[0], parts=1), fc_derivative(g, x[1] - x[0]))
+
+
+def test_subdomain_derivative_reproduces_low_degree_polynomials():
+    """Each segment's FC reproduces polynomials of degree < d = 5 (their
+    continuation is exact to table accuracy), so the decomposed derivative of
+    a global quartic is exact at every point, fringes or not."""
+    from oracle.fcgram import fc_derivative_parts
+    x = np.linspace(-1.0, 1.5, 97)
+    h = x[1] - x[0]
+    p = 0.3 - 1.2 * x + 0.7 * x ** 2 + 0.25 * x ** 3 - 0.4 * x ** 4
+    dp = -1.2 + 1.4 * x + 0.75 * x ** 2 - 1.6 * x ** 3
+    for parts in (2, 3, 5):
+        d = fc_derivative_parts(p, h, parts=parts)
+        assert np.abs(d - dp).max() < 1e-8 * np.abs(dp).max(), parts
+
+
+def test_subdomain_derivative_converges():
+    """Smooth function, 4 parts: the error falls at high order under
+    refinement (each segment keeps the FC accuracy of Sec. 4.3)."""
+    from oracle.fcgram import fc_derivative_parts
+    errs = []
+    ns = (81, 161, 321)
+    for n in ns:
+        x = np.linspace(0.0, 3.0, n)
+        f = np.exp(np.sin(2 * x)) + np.cos(5 * x)
+        df = 2 * np.cos(2 * x) * np.exp(np.sin(2 * x)) - 5 * np.sin(5 * x)
+        d = fc_derivative_parts(f, x[1] - x[0], parts=4)
+        errs.append(np.abs(d - df).max())
+    orders = [np.log(errs[k] / errs[k + 1]) / np.log((ns[k + 1] - 1) / (ns[k] - 1)) for k in range(2)]
+    assert min(orders) > 3.5, (errs, orders)
