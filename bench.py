@@ -257,10 +257,11 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
-    def time_form(precision, steps, warmup, clocks=None):
+    def time_form(precision, steps, warmup, clocks=None, fc_parts=(1, 1)):
         """Forward solve + detector readout per step; CUDA events on the
         launching stream; L2 flushed before every timed step."""
-        solver = FCDOMSolver(g, wl.optics, a, b, wl.c, wl.dt, ckpt_interval=0, precision=precision)
+        solver = FCDOMSolver(g, wl.optics, a, b, wl.c, wl.dt, ckpt_interval=0, precision=precision,
+                             fc_parts=fc_parts)
         schedule = "one-tile" if args.no_autotune else args.schedule
         if precision == B.RTE_PREC_FP32:
             tuned = (1, {})
@@ -334,8 +335,9 @@ def run_ours(args):
     # The other forms on the same workload: the plain FP32 SIMT form (the
     # metric's comparison) and the single-product TF32 reduced-precision form.
     forms = {}
-    for name, prec in (("plain_fp32_simt", B.RTE_PREC_FP32), ("tf32_reduced", B.RTE_PREC_TF32)):
-        s2, ms2, _, _, _, _, _ = time_form(prec, 1, 1)
+    for name, prec, parts in (("plain_fp32_simt", B.RTE_PREC_FP32, (1, 1)), ("tf32_reduced", B.RTE_PREC_TF32, (1, 1)),
+                              ("tf32x3_subdomains_4x4", B.RTE_PREC_TF32X3, (4, 4))):
+        s2, ms2, _, _, _, _, _ = time_form(prec, 1, 1, fc_parts=parts)
         s2.close()
         ms2 = max_over_ranks(ms2)
         forms[name] = {"value": updates * world / (ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2,

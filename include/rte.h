@@ -98,12 +98,22 @@ typedef struct rte_optics {
  * context's stream by events, so the call stays asynchronous on that stream.
  * Off while per-kernel timing is on. */
 #define RTE_FLAG_CUDA_GRAPH 2
+/* fc_parts_x, fc_parts_y: the subdomain decomposition of Sec. 4.4 /
+ * Algorithm 1 along each axis (0 or 1: one domain).  With P parts the n
+ * points of a line are split into P owned ranges [k n / P, (k + 1) n / P);
+ * each part continues and differentiates (eq. RTEFCSumder) its own segment,
+ * the owned range plus two fringe points on every interior side, and a
+ * point's derivative is its owner's (the fringe exchange of Algorithm 1).
+ * The decomposed derivative is a different linear map from the global one;
+ * it is built in FP64 on the host like the global operator and applied by
+ * the same kernels.  Every segment must have at least 16 points. */
 typedef struct rte_params {
   double dt;
   double filter_alpha, filter_beta;
   int ckpt_interval;
   int precision;
   int flags;
+  int fc_parts_x, fc_parts_y;
 } rte_params;
 
 /* One laser beam s_k of eq. (RTEsources2): position (x, y) on the boundary,
@@ -222,6 +232,10 @@ rte_status rte_get_state(rte_ctx* ctx, int group, float* out);
  * rte_host_phase_matrix writes P~[m*M + q] = w p_{m,q} normalised as in
  * Sec. 4.1.  Errors: INVALID_ARG. */
 rte_status rte_host_fc_operator(int n, double h, double alpha, double beta, double* D_out);
+/* The decomposed operator of rte_params.fc_parts_x / fc_parts_y for one
+ * line (parts >= 1, every segment at least 16 points).  Errors: INVALID_ARG. */
+rte_status rte_host_fc_operator_parts(int n, double h, double alpha, double beta, int parts,
+                                      double* D_out);
 rte_status rte_host_phase_matrix(int M, double g, double exponent, double* P_out);
 
 /* Per-kernel timing with CUDA events on the context's stream.  While on,

@@ -35,7 +35,8 @@ class RteOptics(ctypes.Structure):
 
 class RteParams(ctypes.Structure):
     _fields_ = [("dt", c_double), ("filter_alpha", c_double), ("filter_beta", c_double),
-                ("ckpt_interval", c_int), ("precision", c_int), ("flags", c_int)]
+                ("ckpt_interval", c_int), ("precision", c_int), ("flags", c_int),
+                ("fc_parts_x", c_int), ("fc_parts_y", c_int)]
 
 
 class RteBeam(ctypes.Structure):
@@ -66,7 +67,7 @@ EXPORTS = ("rte_init_medium", "rte_set_medium", "rte_forward", "rte_detector_rea
            "rte_destroy", "rte_status_string", "rte_host_fc_operator", "rte_host_phase_matrix",
            "rte_set_kernel_timing", "rte_kernel_times", "rte_forward_static", "rte_forward_batch",
            "rte_graph_captures", "rte_set_pass_variant", "rte_last_cuda_error",
-           "rte_autotune")
+           "rte_autotune", "rte_host_fc_operator_parts")
 
 _lib = None
 
@@ -95,6 +96,7 @@ def library() -> ctypes.CDLL:
         "rte_status_string": [c_int],
         "rte_host_fc_operator": [c_int, c_double, c_double, c_double, P],
         "rte_host_phase_matrix": [c_int, c_double, c_double, P],
+        "rte_host_fc_operator_parts": [c_int, c_double, c_double, c_double, c_int, P],
         "rte_set_kernel_timing": [P, c_int],
         "rte_kernel_times": [P, POINTER(c_double), POINTER(c_longlong)],
         "rte_forward_static": [P, POINTER(RteSourceGroup), c_int, c_int, POINTER(RteDetector), c_int, P],
@@ -251,6 +253,15 @@ def rte_get_state(ctx, group: int, out):
 
 def rte_kernel_launches(ctx) -> int:
     return int(library().rte_kernel_launches(ctx))
+
+
+def rte_host_fc_operator_parts(n: int, h: float, parts: int, alpha: float = 2.0, beta: float = 55.0):
+    """Host FP64 decomposed FC derivative operator (numpy n x n), Sec. 4.4."""
+    import numpy as np
+    out = np.zeros((n, n), dtype=np.float64)
+    _check(library().rte_host_fc_operator_parts(n, h, alpha, beta, int(parts), c_void_p(out.ctypes.data)),
+           "rte_host_fc_operator_parts")
+    return out
 
 
 def rte_host_fc_operator(n: int, h: float, alpha: float = 2.0, beta: float = 55.0):

@@ -542,6 +542,14 @@ rte_status rte_host_fc_operator(int n, double h, double alpha, double beta, doub
   return RTE_OK;
 }
 
+rte_status rte_host_fc_operator_parts(int n, double h, double alpha, double beta, int parts, double* D_out) {
+  if (n < 16 || n > 4096 || !(h > 0) || !D_out || parts < 1) return RTE_ERR_INVALID_ARG;
+  std::vector<double> Dm;
+  if (!rte_setup::fc_derivative_matrix_parts(n, h, alpha, beta, parts, Dm)) return RTE_ERR_INVALID_ARG;
+  std::memcpy(D_out, Dm.data(), Dm.size() * sizeof(double));
+  return RTE_OK;
+}
+
 rte_status rte_host_phase_matrix(int M, double g, double exponent, double* P_out) {
   if (M < 2 || !P_out || !(std::fabs(g) < 1.0)) return RTE_ERR_INVALID_ARG;
   std::vector<double> P;
@@ -600,7 +608,7 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
   if (!(g->xmax > g->xmin) || !(g->ymax > g->ymin)) return RTE_ERR_INVALID_ARG;
   if (!(p->dt > 0) || !(o->c > 0) || !(o->n_in > 0) || !(o->n_out > 0) || std::fabs(o->g) >= 1.0 ||
       p->ckpt_interval < 0 || (p->flags & ~(RTE_FLAG_TC_SCATTER | RTE_FLAG_CUDA_GRAPH)) != 0 ||
-      p->precision < RTE_PREC_FP32 || p->precision > RTE_PREC_BF16)
+      p->precision < RTE_PREC_FP32 || p->precision > RTE_PREC_BF16 || p->fc_parts_x < 0 || p->fc_parts_y < 0)
     return RTE_ERR_INVALID_ARG;
   if (p->precision != RTE_PREC_FP32 && !rte_kern::tc_supported(g->nx, g->ny, g->M, p->precision, p->flags))
     return RTE_ERR_UNSUPPORTED;
@@ -622,10 +630,12 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
   std::vector<double> Dm;
   const int dims[2] = {g->nx, g->ny};
   const double hs[2] = {c->dx, c->dy};
+  const int parts[2] = {p->fc_parts_x, p->fc_parts_y};
   DevBuf* dst[2] = {&c->DxT, &c->DyT};
   for (int ax = 0; ax < 2; ++ax) {
     const int n = dims[ax];
-    rte_setup::fc_derivative_matrix(n, hs[ax], p->filter_alpha, p->filter_beta, Dm);
+    if (!rte_setup::fc_derivative_matrix_parts(n, hs[ax], p->filter_alpha, p->filter_beta, parts[ax], Dm))
+      return fail(RTE_ERR_INVALID_ARG);
     std::vector<float> T(static_cast<size_t>(n) * n);
     for (int i = 0; i < n; ++i)
       for (int k = 0; k < n; ++k) T[static_cast<size_t>(k) * n + i] = static_cast<float>(Dm[static_cast<size_t>(i) * n + k]);
@@ -647,8 +657,8 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
       if (s != RTE_OK) return fail(s);
     }
   }
-  c->rho_dx = rte_setup::fc_spectral_radius(g->nx, c->dx, p->filter_alpha, p->filter_beta);
-  c->rho_dy = rte_setup::fc_spectral_radius(g->ny, c->dy, p->filter_alpha, p->filter_beta);
+  c->rho_dx = rte_setup::fc_spectral_radius_parts(g->nx, c->dx, p->filter_alpha, p->filter_beta, p->fc_parts_x);
+  c->rho_dy = rte_setup::fc_spectral_radius_parts(g->ny, c->dy, p->filter_alpha, p->filter_beta, p->fc_parts_y);
 
   // Phase matrix (Sec. 4.1), transposed: PT[q*M + m] = P~[m][q].
   std::vector<double> P;

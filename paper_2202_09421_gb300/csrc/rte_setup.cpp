@@ -2,6 +2,7 @@
 // boundary tables.  See rte_setup.h.
 #include "rte_setup.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -66,6 +67,50 @@ void fc_derivative_matrix(int n, double h, double alpha, double beta,
       }
     }
   }
+}
+
+namespace {
+constexpr int kFringe = 2;   // fringe points on each interior side (Sec. 4.4)
+
+// Owned range [lo, hi) and segment [slo, shi) of part k of `parts`.
+void part_range(int n, int parts, int k, int& lo, int& hi, int& slo, int& shi) {
+  lo = static_cast<int>(static_cast<long long>(k) * n / parts);
+  hi = static_cast<int>(static_cast<long long>(k + 1) * n / parts);
+  slo = k > 0 ? lo - kFringe : lo;
+  shi = k < parts - 1 ? hi + kFringe : hi;
+}
+}  // namespace
+
+bool fc_derivative_matrix_parts(int n, double h, double alpha, double beta, int parts,
+                                std::vector<double>& D) {
+  if (parts <= 1) {
+    fc_derivative_matrix(n, h, alpha, beta, D);
+    return true;
+  }
+  D.assign(static_cast<size_t>(n) * n, 0.0);
+  std::vector<double> Ds;
+  for (int k = 0; k < parts; ++k) {
+    int lo, hi, slo, shi;
+    part_range(n, parts, k, lo, hi, slo, shi);
+    const int ns = shi - slo;
+    if (ns < 16) return false;
+    fc_derivative_matrix(ns, h, alpha, beta, Ds);
+    for (int i = lo; i < hi; ++i)
+      for (int j = 0; j < ns; ++j)
+        D[static_cast<size_t>(i) * n + slo + j] = Ds[static_cast<size_t>(i - slo) * ns + j];
+  }
+  return true;
+}
+
+double fc_spectral_radius_parts(int n, double h, double alpha, double beta, int parts) {
+  if (parts <= 1) return fc_spectral_radius(n, h, alpha, beta);
+  double best = 0.0;
+  for (int k = 0; k < parts; ++k) {
+    int lo, hi, slo, shi;
+    part_range(n, parts, k, lo, hi, slo, shi);
+    best = std::max(best, fc_spectral_radius(shi - slo, h, alpha, beta));
+  }
+  return best;
 }
 
 // Round an FP32 value to tf32 (10-bit mantissa), nearest with ties away

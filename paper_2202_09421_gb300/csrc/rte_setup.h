@@ -18,6 +18,17 @@ int smooth5(int n);
 void fc_derivative_matrix(int n, double h, double alpha, double beta,
                           std::vector<double>& D);
 
+// The decomposed operator of Sec. 4.4 / Algorithm 1: the n points split
+// into `parts` owned ranges [k n / parts, (k + 1) n / parts), each extended
+// by two fringe points on interior sides; row i of D is the row of i's owner
+// in the FC operator of the owner's segment (columns of that segment).
+// parts <= 1 is fc_derivative_matrix.  Returns false if a segment has fewer
+// than 16 points.
+bool fc_derivative_matrix_parts(int n, double h, double alpha, double beta, int parts,
+                                std::vector<double>& D);
+// Largest spectral-radius estimate over the segments of a decomposition.
+double fc_spectral_radius_parts(int n, double h, double alpha, double beta, int parts);
+
 // Split, pre-swizzled image of D for the tcgen05 kernels: for every chunk q
 // of 32 input positions, a hi tile then a lo tile, each n_rows (= n rounded
 // up to 128) rows x 32 tf32 values in the K-major 128-byte-swizzle order

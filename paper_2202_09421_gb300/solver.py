@@ -15,7 +15,7 @@ class FCDOMSolver:
 
     def __init__(self, grid, optics, mua: torch.Tensor, mus: torch.Tensor, c: float, dt: float,
                  ckpt_interval: int = 0, filter_alpha: float = 2.0, filter_beta: float = 55.0,
-                 stream=None, precision: int = 0, flags: int = 0):
+                 stream=None, precision: int = 0, flags: int = 0, fc_parts=(1, 1)):
         self.grid = grid
         self.device = mua.device
 
@@ -24,7 +24,8 @@ class FCDOMSolver:
         o = _Opt()
         o.g, o.n_in, o.n_out = optics.g, optics.n_in, optics.n_out
         o.hg_exponent, o.c = optics.hg_exponent, c
-        params = B.RteParams(dt, filter_alpha, filter_beta, int(ckpt_interval), int(precision), int(flags))
+        params = B.RteParams(dt, filter_alpha, filter_beta, int(ckpt_interval), int(precision), int(flags),
+                             int(fc_parts[0]), int(fc_parts[1]))
         self.ctx = B.rte_init_medium(grid, mua.contiguous(), mus.contiguous(), o, params, stream)
         self.n_groups = 0
         self.n_steps = 0

@@ -98,3 +98,28 @@ def test_argument_validation_without_device(B):
     assert lib.rte_forward(None, None, 0, 0, None, 0, None) == 1
     assert lib.rte_destroy(None) == 1
     assert B.rte_status_string(2).startswith("dt outside")
+
+
+@pytest.mark.parametrize("n,h,parts", [(64, 0.05, 2), (97, 0.02, 3), (256, 4 / 255, 4), (200, 0.03, 5)])
+def test_host_decomposed_operator_matches_oracle(B, n, h, parts):
+    """The library's decomposed operator (Sec. 4.4, built from its own
+    FC-Gram table and closed-form kernel) against the oracle's per-segment
+    FFT derivative applied to the identity."""
+    from oracle.fcgram import fc_derivative_parts
+    D = B.rte_host_fc_operator_parts(n, h, parts)
+    Do = fc_derivative_parts(np.eye(n), h, axis=-1, parts=parts).T
+    scale = np.abs(Do).max()
+    # Segments of 34-66 points: the two FP64 routes (closed-form kernel sums
+    # against FFT) already differ by 1.04e-12 relative on a global line of 34
+    # points, the level of these short lines.
+    assert np.abs(D - Do).max() <= 4e-12 * scale
+    # block structure: row i has support only in its owner's segment
+    from oracle.fcgram import subdomain_segments
+    for lo, hi, slo, shi in subdomain_segments(n, parts):
+        assert np.all(D[lo:hi, :slo] == 0) and np.all(D[lo:hi, shi:] == 0)
+
+
+def test_host_decomposed_operator_rejects_short_segments(B):
+    with pytest.raises(B.RTEError) as err:
+        B.rte_host_fc_operator_parts(40, 0.05, 4)      # owned ranges of 10 -> segments of 12-14 points
+    assert err.value.status == 1
