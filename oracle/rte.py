@@ -360,6 +360,109 @@ class Solver:
         wy[[0, -1]] *= 0.5
         return wy[:, None] * wx[None, :]
 
+    # --- exact discrete adjoint (the transpose of the discrete march) --------
+    def _dense_derivatives(self):
+        """Dense x and y FC operators (D g = derivative of g) of this solver's
+        (possibly decomposed) derivative, built by applying it to the identity."""
+        if not hasattr(self, "_Dx"):
+            g = self.grid
+            self._Dx = fcgram.fc_derivative_parts(np.eye(g.nx), g.dx, axis=-1, parts=self.fc_parts[0],
+                                                  tables=self.tables).T
+            self._Dy = fcgram.fc_derivative_parts(np.eye(g.ny), g.dy, axis=-1, parts=self.fc_parts[1],
+                                                  tables=self.tables).T
+        return self._Dx, self._Dy
+
+    def L_transpose(self, v):
+        """Transpose of the linear map u -> L(u) of eq. (RTEAB4L) on v[m, j, i]:
+        b P^T v - (a + b) v - xi_m D_x^T v - eta_m D_y^T v."""
+        Dx, Dy = self._dense_derivatives()
+        dxT = np.tensordot(v, Dx, axes=([2], [0]))                  # sum_k v[m, j, k] D_x[k, i]
+        dyT = np.einsum("kj,mki->mji", Dy, v)                       # sum_k D_y[k, j] v[m, k, i]
+        return (self.b * np.tensordot(self.P.T, v, axes=(1, 0)) - (self.a + self.b) * v
+                - self.xi[:, None, None] * dxT - self.eta[:, None, None] * dyT)
+
+    def bc_transpose(self, ubar):
+        """Transpose of the linear part of apply_bc (the source term does not
+        depend on the field): an active (node, m) takes f times the pre-BC
+        value of ordinate refl(m), every other entry keeps its own value."""
+        bt = self.bt
+        out = ubar.copy()
+        ob = ubar[:, bt.nodes_j, bt.nodes_i].T                      # [node, m]
+        pre_bar = np.where(bt.active, 0.0, ob)
+        contrib = np.where(bt.active, bt.fcoef * ob, 0.0)
+        np.add.at(pre_bar, (np.arange(ob.shape[0])[:, None], bt.refl), contrib)
+        out[:, bt.nodes_j, bt.nodes_i] = pre_bar.T
+        return out
+
+    def _exit_weights(self):
+        wl = self.wl
+        return [np.where(cosv > TIE_TOL, self.w * (1 - fresnel(cosv, wl.optics.n_in, wl.optics.n_out)) * cosv, 0.0)
+                for cosv in self.bt.face_cos]
+
+    def readout_transpose(self, rs, W, wts):
+        """Transpose of u -> dt-weighted curves of one recorded level
+        (exitance of eq. OpMed, then the detector sums) applied to the
+        residuals rs[det]."""
+        ub = np.zeros((self.M, self.grid.ny, self.grid.nx))
+        for F, (jj, ii, _) in enumerate(self.bt.face_nodes):
+            e_bar = (W[F].T @ rs) * self.dt                          # [node]
+            np.add.at(ub, (slice(None), jj, ii), wts[F][:, None] * e_bar[None, :])
+        return ub
+
+    def discrete_adjoint_gradient(self, beams, n_steps, detectors, measured):
+        """Exact gradient of the discrete objective (eq. FObj with the
+        rectangle rule over the recorded levels) with respect to the nodal
+        values of a and b: the reverse sweep of the discrete march (AB4,
+        boundary condition, exitance, readout), with the transposed FC
+        operators.  Returns (J, dJ/da [ny, nx], dJ/db [ny, nx])."""
+        fwd = self.forward(beams, n_steps, detectors, keep_states=True)
+        r = fwd["curves"] - measured                                 # [det, step]
+        J = self.objective(fwd["curves"], measured)
+        states = [np.zeros_like(fwd["states"][0])] + fwd["states"]  # u^0 .. u^N
+        W = self.detector_weights(detectors)
+        wts = self._exit_weights()
+        cdt = self.c * self.dt
+        ubar = self.readout_transpose(r[:, n_steps - 1], W, wts)     # adjoint of u^N
+        Lbar = {}
+        ga = np.zeros((self.grid.ny, self.grid.nx))
+        gb = np.zeros_like(ga)
+        for s in range(n_steps - 1, -1, -1):
+            # step s: u^{s+1} = BC(u^s + c dt sum_i chi_i L^{s-i})
+            utb = self.bc_transpose(ubar)
+            for i in range(4):
+                if s - i >= 0:
+                    Lbar[s - i] = Lbar.get(s - i, 0.0) + cdt * AB4[i] * utb
+            Lb = Lbar.pop(s)                                         # complete: steps s..s+3 are done
+            u_s = states[s]
+            ubar = utb + self.L_transpose(Lb)
+            if s >= 1:
+                ubar = ubar + self.readout_transpose(r[:, s - 1], W, wts)
+            ga -= (Lb * u_s).sum(axis=0)
+            gb += (Lb * (self.scatter(u_s) - u_s)).sum(axis=0)
+        return J, ga, gb
+
+    def tangent_linear_objective(self, beams, n_steps, detectors, measured, da, db):
+        """Forward-mode derivative of the discrete objective in the direction
+        (da, db) of nodal perturbations of a and b (the tangent-linear march;
+        an independent check of the discrete adjoint)."""
+        fwd = self.forward(beams, n_steps, detectors, keep_states=True)
+        r = fwd["curves"] - measured
+        states = [np.zeros_like(fwd["states"][0])] + fwd["states"]
+        cdt = self.c * self.dt
+        du = np.zeros_like(states[0])
+        dh = [np.zeros_like(du) for _ in range(3)]
+        zero_q = np.zeros((len(self.bx), self.M))
+        dJ = 0.0
+        for s in range(n_steps):
+            u_s = states[s]
+            dL = self.L(du) - da * u_s + db * (self.scatter(u_s) - u_s)
+            du = du + cdt * (AB4[0] * dL + AB4[1] * dh[0] + AB4[2] * dh[1] + AB4[3] * dh[2])
+            self.apply_bc(du, zero_q)
+            dh = [dL, dh[0], dh[1]]
+            dG = self.readout([e[:, None] for e in self.exitance(du)], detectors)[:, 0]
+            dJ += float(np.sum(r[:, s] * dG)) * self.dt
+        return dJ
+
     def adjoint_gradient(self, beams, n_steps, detectors, measured):
         """Forward solve, residual, backward adjoint march of eq.
         (AdjointProblem) and the gradient of eq. (FDwin22) per grid node.
