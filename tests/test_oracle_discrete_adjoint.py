@@ -45,19 +45,23 @@ def test_discrete_adjoint_matches_central_differences():
     J, ga, gb = S.discrete_adjoint_gradient(wl.groups[0], wl.n_steps, wl.detectors, meas[0])
     rng = np.random.default_rng(3)
     da = rng.standard_normal(ga.shape)
-    eps = 1e-4        # truncation ~1e-5 relative here; rounding of J below it
 
     def J_of(mua):
         Sp = Solver(dataclasses.replace(wl, mua=mua))
         return Sp.objective(Sp.forward(wl.groups[0], wl.n_steps, wl.detectors)["curves"], meas[0])
 
+    # J is nearly linear in a over this range, while the rounding of the
+    # FFT-based march adds noise of ~1e-11 relative to J, which central
+    # differences divide by eps: their error falls from 2e-3 at eps = 1e-6
+    # to 1.6e-7 at eps = 1e-2, so the large step is the accurate one.
+    eps = 1e-2
     fd = (J_of(wl.mua + eps * da) - J_of(wl.mua - eps * da)) / (2 * eps)
     rel = abs(fd - float((ga * da).sum())) / abs(fd)
-    print(f"discrete adjoint vs central difference: {rel:.1e}")
-    assert rel < 1e-4
+    print(f"discrete adjoint vs central differences: {rel:.1e}")
+    assert rel < 1e-5
     # a single node, well inside: the exact nodal derivative
     j, i = wl.grid.ny // 2, wl.grid.nx // 2
     e = np.zeros_like(ga)
     e[j, i] = 1.0
-    fd1 = (J_of(wl.mua + 1e-3 * e) - J_of(wl.mua - 1e-3 * e)) / 2e-3
-    assert abs(fd1 - ga[j, i]) < 1e-4 * abs(ga).max()
+    fd1 = (J_of(wl.mua + 1e-2 * e) - J_of(wl.mua - 1e-2 * e)) / 2e-2
+    assert abs(fd1 - ga[j, i]) < 1e-5 * abs(ga).max()
