@@ -388,7 +388,19 @@ def run_ours(args):
             torch.cuda.synchronize()
             gt.append(time.perf_counter() - t0)
         gs = max_over_ranks(gt[-1])
+        # the exact discrete adjoint (transposed march) on the same workload
+        dt_ = []
+        for k in range(2):
+            flush.fill_(float(k))
+            barrier()
+            t0 = time.perf_counter()
+            sa.forward(wm.groups, wm.n_steps)
+            J, ga, gb = sa.discrete_adjoint_gradient(wm.detectors, measured)
+            torch.cuda.synchronize()
+            dt_.append(time.perf_counter() - t0)
+        ds = max_over_ranks(dt_[-1])
         adjoint = {"gradients_per_s": world / gs, "seconds_per_gradient": gs,
+                   "discrete_gradients_per_s": world / ds, "seconds_per_discrete_gradient": ds,
                    "workload": "mss256_M32: 256x256, M=32, 4 MSS groups x 4 beams, 3000 steps, "
                                "checkpoint every 100, 32 detectors",
                    "update_equivalents_per_gradient": 3 * wm.updates}

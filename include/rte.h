@@ -220,6 +220,26 @@ rte_status rte_adjoint_gradient(rte_ctx* ctx, const rte_detector* dets, int n_de
                                 const float* measured, double* J_out,
                                 float* dJ_dmua, float* dJ_dmus);
 
+/* Objective and the exact gradient of the discrete objective: the same J as
+ * rte_adjoint_gradient, and dJ/dmua, dJ/dmus with respect to the nodal values
+ * of a and b of the discrete march itself (AB4 of eq. RTEAB4, the boundary
+ * map of eq. RTE, the exitance of eq. OpMed and the rectangle rule of eq.
+ * FObj), summed over groups, device FP32 [ny][nx] each (either may be NULL):
+ *   dJ/dmua = -sum_s sum_m v^s u^s,  dJ/dmus = sum_s sum_m v^s (P~u^s - u^s),
+ * where v^s is the adjoint of the AB4 increment of level s, found by the
+ * reverse sweep of the march (the transposed FC operators D_x^T, D_y^T of
+ * Sec. 4.3, the transposed boundary map and readout, the AB4 weights applied
+ * backwards).  Unlike the continuous adjoint of eq. (AdjointProblem) it
+ * agrees with finite differences of J to rounding, not to discretisation
+ * level.  Arguments, ownership and synchronisation as rte_adjoint_gradient;
+ * the transposed operators are built on the first call.  The passes run in
+ * the context's precision with the one-tile-per-CTA schedule.
+ * Errors: INVALID_ARG, STATE (no forward, or ckpt_interval == 0), OOM, CUDA,
+ * TIMEOUT (tensor-core forms). */
+rte_status rte_discrete_adjoint_gradient(rte_ctx* ctx, const rte_detector* dets, int n_det,
+                                         const float* measured, double* J_out,
+                                         float* dJ_dmua, float* dJ_dmus);
+
 /* Copies the current AB4 state of group g (u after the last step, FP32
  * [ny][nx][M]) into out (device).  Diagnostic; INVALID_ARG, STATE. */
 rte_status rte_get_state(rte_ctx* ctx, int group, float* out);

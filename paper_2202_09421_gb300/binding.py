@@ -67,7 +67,7 @@ EXPORTS = ("rte_init_medium", "rte_set_medium", "rte_forward", "rte_detector_rea
            "rte_destroy", "rte_status_string", "rte_host_fc_operator", "rte_host_phase_matrix",
            "rte_set_kernel_timing", "rte_kernel_times", "rte_forward_static", "rte_forward_batch",
            "rte_graph_captures", "rte_set_pass_variant", "rte_last_cuda_error",
-           "rte_autotune", "rte_host_fc_operator_parts")
+           "rte_autotune", "rte_host_fc_operator_parts", "rte_discrete_adjoint_gradient")
 
 _lib = None
 
@@ -90,6 +90,7 @@ def library() -> ctypes.CDLL:
         "rte_detector_readout": [P, POINTER(RteDetector), c_int, P],
         "rte_objective": [P, POINTER(RteDetector), c_int, P, POINTER(c_double)],
         "rte_adjoint_gradient": [P, POINTER(RteDetector), c_int, P, POINTER(c_double), P, P],
+        "rte_discrete_adjoint_gradient": [P, POINTER(RteDetector), c_int, P, POINTER(c_double), P, P],
         "rte_get_state": [P, c_int, P],
         "rte_kernel_launches": [P],
         "rte_destroy": [P],
@@ -244,6 +245,15 @@ def rte_adjoint_gradient(ctx, dets, measured, dJ_dmua=None, dJ_dmus=None) -> flo
                                           _dev_ptr(measured, "measured"), ctypes.byref(J),
                                           _dev_ptr(dJ_dmua, "dJ_dmua"), _dev_ptr(dJ_dmus, "dJ_dmus")),
            "rte_adjoint_gradient")
+    return J.value
+
+
+def rte_discrete_adjoint_gradient(ctx, dets, measured, dJ_dmua=None, dJ_dmus=None) -> float:
+    J = c_double()
+    _check(library().rte_discrete_adjoint_gradient(ctx, make_detectors(dets), len(dets),
+                                                   _dev_ptr(measured, "measured"), ctypes.byref(J),
+                                                   _dev_ptr(dJ_dmua, "dJ_dmua"), _dev_ptr(dJ_dmus, "dJ_dmus")),
+           "rte_discrete_adjoint_gradient")
     return J.value
 
 

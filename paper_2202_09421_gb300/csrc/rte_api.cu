@@ -33,6 +33,10 @@ struct rte_ctx {
   DevBuf DxT, DyT, PT, xi, eta, mua, mus, area;
   DevBuf face_refl, corner_refl, face_f, corner_f, face_act, corner_act, wexit;
   DevBuf DxImg, DyImg, PImg;       // split, swizzled operators (tensor-core forms)
+  // transposed operators D_x^T, D_y^T and the transposed boundary map of the
+  // exact discrete adjoint (built on its first use)
+  DevBuf DxTt, DyTt, DxImgT, DyImgT, bct_src, bct_f;
+  bool transposed_ready = false;
   int tc_mode = 0;                 // the precision: 0 SIMT FP32, 1-4 tcgen05 forms
   int x_variant = 1;               // pass kernels: 0 persistent warp-specialised, 1 one tile per CTA, 2 pipelined y-pass
   // state of the last forward
@@ -173,6 +177,8 @@ rte_kern::BoundaryArgs boundary_args(rte_ctx* c) {
   b.kmax = 0; b.T_len = 0;
   b.rho = nullptr; b.rho_len = 0;
   b.ring_out = nullptr; b.ring_steps = 0;
+  b.bct_src = nullptr; b.bct_f = nullptr;
+  b.ebar = nullptr; b.ebar_len = 0;
   return b;
 }
 
@@ -256,6 +262,58 @@ rte_status march(rte_ctx* c, DevBuf& U, DevBuf& R, DevBuf* L, int& hl, int G, in
       RTE_TRY(cuda_status(cudaMemcpyAsync((*seg_out)[s - s_begin], U.p, gbytes,
                                           cudaMemcpyDeviceToDevice, c->stream)));
   }
+  return RTE_OK;
+}
+
+// Uploads the operator E (row-major n x n, FP64) in the kernels' forms: the
+// SIMT array ET[k n + i] = E[i][k] and, in the tensor-core forms, the split,
+// swizzled image (synchronises: the host vectors must outlive the copies).
+rte_status upload_operator(rte_ctx* c, const std::vector<double>& E, int n, DevBuf& simt, DevBuf& img) {
+  std::vector<float> T(static_cast<size_t>(n) * n);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) T[static_cast<size_t>(k) * n + i] = static_cast<float>(E[static_cast<size_t>(i) * n + k]);
+  RTE_TRY(upload(simt, T, c->stream));
+  std::vector<float> im;
+  std::vector<unsigned short> im16;
+  if (c->tc_mode == RTE_PREC_BF16X3 || c->tc_mode == RTE_PREC_BF16) {
+    rte_setup::tc_operator_image_bf16(E, n, im16);
+    RTE_TRY(upload(img, im16, c->stream));
+  } else if (c->tc_mode != 0) {
+    rte_setup::tc_operator_image(E, n, im);
+    RTE_TRY(upload(img, im, c->stream));
+  }
+  return cuda_status(cudaStreamSynchronize(c->stream));
+}
+
+// D_x^T, D_y^T and the transposed boundary tables of the exact discrete
+// adjoint, built once per context.
+rte_status ensure_transposed(rte_ctx* c) {
+  if (c->transposed_ready) return RTE_OK;
+  const int dims[2] = {c->nx, c->ny};
+  const double hs[2] = {c->dx, c->dy};
+  const int parts[2] = {c->par.fc_parts_x, c->par.fc_parts_y};
+  DevBuf* simt[2] = {&c->DxTt, &c->DyTt};
+  DevBuf* img[2] = {&c->DxImgT, &c->DyImgT};
+  std::vector<double> Dm, Dt;
+  for (int ax = 0; ax < 2; ++ax) {
+    const int n = dims[ax];
+    if (!rte_setup::fc_derivative_matrix_parts(n, hs[ax], c->par.filter_alpha, c->par.filter_beta, parts[ax], Dm))
+      return RTE_ERR_INVALID_ARG;
+    Dt.assign(Dm.size(), 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int k = 0; k < n; ++k) Dt[static_cast<size_t>(k) * n + i] = Dm[static_cast<size_t>(i) * n + k];
+    RTE_TRY(upload_operator(c, Dt, n, *simt[ax], *img[ax]));
+  }
+  rte_setup::BoundaryTables bt;
+  rte_setup::boundary_tables(c->M, c->opt.n_in, c->opt.n_out, bt);
+  std::vector<int> src;
+  std::vector<double> f;
+  if (!rte_setup::bc_transpose_tables(bt, c->M, src, f)) return RTE_ERR_UNSUPPORTED;
+  RTE_TRY(upload(c->bct_src, src, c->stream));
+  std::vector<float> f32 = to_f32(f);
+  RTE_TRY(upload(c->bct_f, f32, c->stream));
+  RTE_TRY(cuda_status(cudaStreamSynchronize(c->stream)));
+  c->transposed_ready = true;
   return RTE_OK;
 }
 
@@ -567,7 +625,8 @@ rte_status rte_destroy(rte_ctx* c) {
                    &c->ring, &c->S, &c->A, &c->T, &c->ckpt, &c->MU, &c->RA, &c->LA[0],
                    &c->LA[1], &c->LA[2], &c->seg, &c->curves64, &c->resid, &c->partial,
                    &c->Jdev, &c->rho, &c->grad_a, &c->grad_b, &c->Wd, &c->Wn, &c->lohi,
-                   &c->DxImg, &c->DyImg, &c->PImg};
+                   &c->DxImg, &c->DyImg, &c->PImg, &c->DxTt, &c->DyTt, &c->DxImgT, &c->DyImgT,
+                   &c->bct_src, &c->bct_f};
   for (DevBuf* b : all) release(*b);
   release(c->batch_tab);
   for (cudaEvent_t e : c->events) cudaEventDestroy(e);
@@ -636,26 +695,8 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
     const int n = dims[ax];
     if (!rte_setup::fc_derivative_matrix_parts(n, hs[ax], p->filter_alpha, p->filter_beta, parts[ax], Dm))
       return fail(RTE_ERR_INVALID_ARG);
-    std::vector<float> T(static_cast<size_t>(n) * n);
-    for (int i = 0; i < n; ++i)
-      for (int k = 0; k < n; ++k) T[static_cast<size_t>(k) * n + i] = static_cast<float>(Dm[static_cast<size_t>(i) * n + k]);
-    rte_status s = upload(*dst[ax], T, c->stream);
+    const rte_status s = upload_operator(c, Dm, n, *dst[ax], ax == 0 ? c->DxImg : c->DyImg);
     if (s != RTE_OK) return fail(s);
-    if (c->tc_mode != 0) {
-      std::vector<float> img;
-      std::vector<unsigned short> img16;
-      if (c->tc_mode == RTE_PREC_BF16X3 || c->tc_mode == RTE_PREC_BF16) {
-        rte_setup::tc_operator_image_bf16(Dm, n, img16);
-        s = upload(ax == 0 ? c->DxImg : c->DyImg, img16, c->stream);
-      } else {
-        rte_setup::tc_operator_image(Dm, n, img);
-        s = upload(ax == 0 ? c->DxImg : c->DyImg, img, c->stream);
-      }
-      if (s != RTE_OK) return fail(s);
-      // the host vector must outlive the asynchronous copy
-      s = cuda_status(cudaStreamSynchronize(c->stream));
-      if (s != RTE_OK) return fail(s);
-    }
   }
   c->rho_dx = rte_setup::fc_spectral_radius_parts(g->nx, c->dx, p->filter_alpha, p->filter_beta, p->fc_parts_x);
   c->rho_dy = rte_setup::fc_spectral_radius_parts(g->ny, c->dy, p->filter_alpha, p->filter_beta, p->fc_parts_y);
@@ -860,12 +901,18 @@ rte_status rte_objective(rte_ctx* c, const rte_detector* dets, int n_det, const 
   return cuda_status(cudaStreamSynchronize(c->stream));
 }
 
-rte_status rte_adjoint_gradient(rte_ctx* c, const rte_detector* dets, int n_det, const float* measured,
-                                double* J_out, float* dJ_dmua, float* dJ_dmus) {
+// Objective and gradient after a forward march: the continuous adjoint of
+// eq. (AdjointProblem) (discrete = false) or the exact discrete adjoint, the
+// transpose of the discrete march (discrete = true).  Both recompute the
+// forward levels segment by segment from the checkpoints, on a second stream,
+// while the adjoint march consumes the previous segment.
+static rte_status adjoint_impl(rte_ctx* c, const rte_detector* dets, int n_det, const float* measured,
+                               double* J_out, float* dJ_dmua, float* dJ_dmus, bool discrete) {
   if (!c || !dets || n_det <= 0 || !measured || !J_out) return RTE_ERR_INVALID_ARG;
   if (c->n_steps <= 0 || c->par.ckpt_interval <= 0) return RTE_ERR_STATE;
   for (int d = 0; d < n_det; ++d)
     if (!(dets[d].sigma_d > 0)) return RTE_ERR_INVALID_ARG;
+  if (discrete) RTE_TRY(ensure_transposed(c));
   const int G = c->G, N = c->n_steps, I = c->par.ckpt_interval;
   const size_t gfloats = static_cast<size_t>(G) * c->plane, gbytes = gfloats * sizeof(float);
   const size_t ncurve = static_cast<size_t>(G) * n_det * N;
@@ -900,7 +947,10 @@ rte_status rte_adjoint_gradient(rte_ctx* c, const rte_detector* dets, int n_det,
                                                n_det, nullptr, D(c->curves64), c->stream, &c->launches)));
   RTE_TRY(cuda_status(rte_kern::launch_objective(D(c->curves64), measured, ncurve, c->par.dt, F(c->resid),
                                                  D(c->partial), D(c->Jdev), c->stream, &c->launches)));
-  RTE_TRY(cuda_status(rte_kern::launch_rho(F(c->resid), F(c->Wn), n_det, c->ring_len, N, G, F(c->rho),
+  // Discrete form: ebar = dt sum_j Wd_j r_j, the transpose of the readout
+  // (trapezoid weights included) applied to dJ/dG = dt r.
+  RTE_TRY(cuda_status(rte_kern::launch_rho(F(c->resid), discrete ? F(c->Wd) : F(c->Wn), n_det, c->ring_len,
+                                           N, G, discrete ? static_cast<float>(c->par.dt) : 1.0f, F(c->rho),
                                            c->stream, &c->launches)));
   RTE_TRY(cuda_status(cudaMemsetAsync(c->grad_a.p, 0, ncell * sizeof(double), c->stream)));
   RTE_TRY(cuda_status(cudaMemsetAsync(c->grad_b.p, 0, ncell * sizeof(double), c->stream)));
@@ -910,8 +960,18 @@ rte_status rte_adjoint_gradient(rte_ctx* c, const rte_detector* dets, int n_det,
   rte_kern::BoundaryArgs bf = boundary_args(c);
   bf.S = F(c->S); bf.A = F(c->A); bf.T = F(c->T); bf.kmax = c->kmax; bf.T_len = N;
   rte_kern::BoundaryArgs ba = boundary_args(c);
-  ba.rho = F(c->rho); ba.rho_len = N;
-  const rte_kern::StepArgs sa = step_args(c, G);
+  rte_kern::StepArgs sa = step_args(c, G);
+  if (discrete) {
+    ba.bct_src = static_cast<const int*>(c->bct_src.p);
+    ba.bct_f = F(c->bct_f);
+    ba.ebar = F(c->rho);
+    ba.ebar_len = N;
+    sa.DxT = F(c->DxTt); sa.DyT = F(c->DyTt);
+    sa.DxImg = c->DxImgT.p; sa.DyImg = c->DyImgT.p;
+    sa.x_variant = 1;
+  } else {
+    ba.rho = F(c->rho); ba.rho_len = N;
+  }
   const double scale = (2.0 * kPi / c->M) * c->par.dt;
   int hl_adj = 0;
   std::vector<int> no_snaps(N, -1);
@@ -959,6 +1019,13 @@ rte_status rte_adjoint_gradient(rte_ctx* c, const rte_detector* dets, int n_det,
     return st;
   };
   if (!segs.empty()) RTE_TRY(recompute(0));
+  // Discrete form: the transposed step with src_step N-1 on the zero state
+  // gives v^{N-1} = c dt chi0 BC^T(readout^T r^{N-1}), the field that the
+  // gradient of level N-1 takes.
+  if (discrete && !segs.empty())
+    RTE_TRY(cuda_status(rte_kern::launch_step(sa, ba, F(c->MU), F(c->RA), F(c->LA[0]), F(c->LA[1]),
+                                              F(c->LA[2]), N - 1, c->stream, &c->launches)));
+  if (discrete) hl_adj = 2;
   for (size_t k = 0; k < segs.size(); ++k) {
     const int seg = segs[k];
     const int s0 = seg * I, s_end = std::min(s0 + I, last + 1);
@@ -970,19 +1037,31 @@ rte_status rte_adjoint_gradient(rte_ctx* c, const rte_detector* dets, int n_det,
     }
     RTE_TRY(cuda_status(cudaStreamWaitEvent(c->stream, done_fwd[k % 2], 0)));
     std::vector<float*> segp = seg_ptrs(static_cast<int>(k), s0, s_end);
-    // Adjoint steps for levels s_end-1 .. s0 (eq. AdjointProblem, flipped).
+    // Adjoint steps for levels s_end-1 .. s0.  Continuous form: the step of
+    // eq. (AdjointProblem) on the flipped field, then its gradient term
+    // (eq. FDwin22, area-weighted).  Discrete form: the gradient term of
+    // level lvl+1 (v^{lvl+1} against u^{lvl+1}, unweighted), then the
+    // transposed step that gives v^{lvl} (not needed at lvl = 0: u^0 = 0).
     for (int lvl = s_end - 1; lvl >= s0; --lvl) {
       float* L1 = F(c->LA[hl_adj]);
       float* L2 = F(c->LA[(hl_adj + 1) % 3]);
       float* L3 = F(c->LA[(hl_adj + 2) % 3]);
-      RTE_TRY(cuda_status(rte_kern::launch_step(sa, ba, F(c->MU), F(c->RA), L1, L2, L3, lvl, c->stream,
-                                                &c->launches)));
-      hl_adj = (hl_adj + 2) % 3;
-      RTE_TRY(cuda_status(rte_kern::launch_grad(F(c->MU), segp[lvl - s0], F(c->PT), F(c->area), c->nx,
-                                                c->ny, c->M, G, c->plane, c->plane, scale,
+      if (!discrete) {
+        RTE_TRY(cuda_status(rte_kern::launch_step(sa, ba, F(c->MU), F(c->RA), L1, L2, L3, lvl, c->stream,
+                                                  &c->launches)));
+        hl_adj = (hl_adj + 2) % 3;
+      }
+      RTE_TRY(cuda_status(rte_kern::launch_grad(F(c->MU), segp[lvl - s0], F(c->PT),
+                                                discrete ? nullptr : F(c->area), c->nx, c->ny, c->M, G,
+                                                c->plane, c->plane, discrete ? 1.0 : scale, discrete ? 0 : 1,
                                                 dJ_dmua ? D(c->grad_a) : nullptr,
                                                 dJ_dmus ? D(c->grad_b) : nullptr, c->stream,
                                                 &c->launches)));
+      if (discrete && lvl >= 1) {
+        RTE_TRY(cuda_status(rte_kern::launch_step(sa, ba, F(c->MU), F(c->RA), L1, L2, L3, lvl, c->stream,
+                                                  &c->launches)));
+        hl_adj = (hl_adj + 2) % 3;
+      }
     }
     RTE_TRY(cuda_status(cudaEventRecord(done_adj[k % 2], c->stream)));
   }
@@ -994,6 +1073,17 @@ rte_status rte_adjoint_gradient(rte_ctx* c, const rte_detector* dets, int n_det,
   RTE_TRY(cuda_status(cudaMemcpyAsync(J_out, c->Jdev.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream)));
   RTE_TRY(cuda_status(cudaStreamSynchronize(c->stream)));
   return tc_check(c);
+}
+
+rte_status rte_adjoint_gradient(rte_ctx* c, const rte_detector* dets, int n_det, const float* measured,
+                                double* J_out, float* dJ_dmua, float* dJ_dmus) {
+  return adjoint_impl(c, dets, n_det, measured, J_out, dJ_dmua, dJ_dmus, false);
+}
+
+rte_status rte_discrete_adjoint_gradient(rte_ctx* c, const rte_detector* dets, int n_det,
+                                         const float* measured, double* J_out, float* dJ_dmua,
+                                         float* dJ_dmus) {
+  return adjoint_impl(c, dets, n_det, measured, J_out, dJ_dmua, dJ_dmus, true);
 }
 
 }  // extern "C"

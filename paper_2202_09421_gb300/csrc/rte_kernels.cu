@@ -13,6 +13,9 @@
 //         eq. (RTEAB4); boundary condition of eq. (RTE) on Gamma_-; exitance
 //         of eq. (OpMed) on the boundary ring.  U is updated in place; the
 //         new L^k overwrites the oldest history slot.
+// The same passes take the transposed step of the exact discrete adjoint
+// (BoundaryArgs::bct_src set): transposed D operators in the GEMMs and the
+// transposed AB4 / boundary / readout bookkeeping in the y-pass epilogue.
 #include <cstdint>
 
 #include "rte_kernels.cuh"
@@ -203,6 +206,12 @@ __global__ void __launch_bounds__(512) ypass_kernel(StepArgs a, BoundaryArgs b, 
     const float l1[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
     const float l2[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
     const float l3[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+    if (b.bct_src) {
+      // transposed step: ubar = w^{k+1} + L^T v (readout term and BC^T below)
+#pragma unroll
+      for (int t = 0; t < kTN; ++t) acc[jj][t] = rv[t] - eta[t] * acc[jj][t] + l1[t];
+      continue;
+    }
     float lk[8];
 #pragma unroll
     for (int t = 0; t < kTN; ++t) {
@@ -234,10 +243,42 @@ __global__ void __launch_bounds__(512) ypass_kernel(StepArgs a, BoundaryArgs b, 
   const int ring_len = 2 * n + 2 * nx;
   for (int cell = warp; cell < n * ncols; cell += nwarps) {
     const int j = cell / ncols, wc = cell - j * ncols, ic = i0 + wc;
-    const float* pre = Bs + j * kTileCols + wc * M;
+    float* pre = Bs + j * kTileCols + wc * M;
     const bool lf = ic == 0, rt = ic == nx - 1, bt = j == 0, tp = j == n - 1;
     const bool bnd = lf || rt || bt || tp;
     float* dst = Ug + (static_cast<size_t>(j) * nx + ic) * M;
+    if (b.bct_src) {
+      // Transposed step on this node: the readout transpose on the ring
+      // (every face the node lies on), w = BC^T ubar, then the transposed
+      // AB4 combination v' = c dt (chi0 w + chi1 w^{k+1} + chi2 w^{k+2} + chi3 w^{k+3}).
+      int tb = -1;
+      if (bnd) {
+        const float* eb = b.ebar + (static_cast<size_t>(g) * b.ebar_len + src_step) * ring_len;
+        for (int m = lane; m < M; m += 32) {
+          float v = pre[m];
+          if (lf || rt) v = fmaf(b.wexit[(lf ? 0 : 1) * M + m], eb[lf ? j : n + j], v);
+          if (bt || tp) v = fmaf(b.wexit[(bt ? 2 : 3) * M + m], eb[bt ? 2 * n + ic : 2 * n + nx + ic], v);
+          pre[m] = v;
+        }
+        __syncwarp();
+        tb = ((lf || rt) && (bt || tp)) ? 4 + (rt ? 1 : 0) + (tp ? 2 : 0) : (lf ? 0 : rt ? 1 : bt ? 2 : 3);
+      }
+      const size_t e0 = goff + (static_cast<size_t>(j) * nx + ic) * M;
+      for (int m = lane; m < M; m += 32) {
+        float wv = pre[m];
+        if (tb >= 0) {
+          const int* src = b.bct_src + (tb * M + m) * 4;
+          const float* cf = b.bct_f + (tb * M + m) * 4;
+          wv = 0.f;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) wv = fmaf(cf[q], pre[src[q]], wv);
+        }
+        const float incr = kAB0 * wv + kAB1 * L1[e0 + m] + kAB2 * L2[e0 + m] + kAB3 * L3[e0 + m];
+        L3[e0 + m] = wv;
+        dst[m] = a.cdt * incr;
+      }
+      continue;
+    }
     if (!bnd) {
       for (int m = lane; m < M; m += 32) dst[m] = pre[m];
       continue;
@@ -359,7 +400,7 @@ __global__ void objective_final(const double* __restrict__ partial, int nb, doub
 }
 
 __global__ void rho_kernel(const float* __restrict__ resid, const float* __restrict__ Wn, int n_det,
-                           int ring_len, int n_steps, int G, float* __restrict__ rho) {
+                           int ring_len, int n_steps, int G, float scale, float* __restrict__ rho) {
   const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   const long long total = static_cast<long long>(G) * n_steps * ring_len;
   if (idx >= total) return;
@@ -370,12 +411,12 @@ __global__ void rho_kernel(const float* __restrict__ resid, const float* __restr
   for (int d = 0; d < n_det; ++d)
     acc = fmaf(Wn[static_cast<size_t>(d) * ring_len + node],
                resid[(static_cast<size_t>(g) * n_det + d) * n_steps + s], acc);
-  rho[idx] = acc;
+  rho[idx] = scale * acc;
 }
 
 __global__ void grad_kernel(const float* __restrict__ MU, const float* __restrict__ Useg,
                             const float* __restrict__ PT, const float* __restrict__ area, int ncell,
-                            int M, int G, size_t plane, size_t useg_gs, double scale,
+                            int M, int G, size_t plane, size_t useg_gs, double scale, int flip,
                             double* __restrict__ grad_a, double* __restrict__ grad_b) {
   __shared__ float ubuf[8][64];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -390,7 +431,7 @@ __global__ void grad_kernel(const float* __restrict__ MU, const float* __restric
     for (int m = lane; m < M; m += 32) {
       float pu = 0.f;
       for (int q = 0; q < M; ++q) pu = fmaf(PT[q * M + m], ubuf[wl][q], pu);
-      const float lam = mu[(m + M / 2) % M];
+      const float lam = flip ? mu[(m + M / 2) % M] : mu[m];
       sa = fmaf(lam, ubuf[wl][m], sa);
       sb = fmaf(lam, ubuf[wl][m] - pu, sb);
     }
@@ -399,7 +440,7 @@ __global__ void grad_kernel(const float* __restrict__ MU, const float* __restric
   sa = warp_sum(sa);
   sb = warp_sum(sb);
   if (lane == 0) {
-    const double k = scale * static_cast<double>(area[cell]);
+    const double k = area ? scale * static_cast<double>(area[cell]) : scale;
     if (grad_a) grad_a[cell] -= k * static_cast<double>(sa);
     if (grad_b) grad_b[cell] -= k * static_cast<double>(sb);
   }
@@ -472,22 +513,23 @@ cudaError_t launch_objective(const double* curves64, const float* measured, size
 }
 
 cudaError_t launch_rho(const float* resid, const float* Wn, int n_det, int ring_len,
-                       int n_steps, int G, float* rho, cudaStream_t s, long long* launches) {
+                       int n_steps, int G, float scale, float* rho, cudaStream_t s,
+                       long long* launches) {
   const long long total = static_cast<long long>(G) * n_steps * ring_len;
   if (total == 0) return cudaSuccess;
   rho_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(resid, Wn, n_det, ring_len,
-                                                                         n_steps, G, rho);
+                                                                         n_steps, G, scale, rho);
   if (launches) *launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_grad(const float* MU, const float* Useg, const float* PT, const float* area,
                         int nx, int ny, int M, int G, size_t plane, size_t useg_group_stride,
-                        double scale, double* grad_a, double* grad_b, cudaStream_t s,
+                        double scale, int flip, double* grad_a, double* grad_b, cudaStream_t s,
                         long long* launches) {
   const int ncell = nx * ny;
   grad_kernel<<<(ncell * 32 + 255) / 256, 256, 0, s>>>(MU, Useg, PT, area, ncell, M, G, plane,
-                                                        useg_group_stride, scale, grad_a, grad_b);
+                                                        useg_group_stride, scale, flip, grad_a, grad_b);
   if (launches) *launches += 1;
   return cudaGetLastError();
 }

@@ -27,6 +27,19 @@ struct BoundaryArgs {
   int rho_len;
   float* ring_out;                  // [G][ring_steps][ring] exitance, or null
   int ring_steps;
+  // Transposed step of the exact discrete adjoint (bct_src non-null).  The
+  // state buffers then hold v (U: the field the transposed operator acts
+  // on) and the history w of transposed boundary values (L1 = w^{k+1},
+  // L2 = w^{k+2}, L3 = w^{k+3}); the x-pass is unchanged (P~ is symmetric)
+  // and the y-pass epilogue forms, with the transposed D operators,
+  //   ubar = L1 + L^T v + readout^T(r^k)          (readout term on ring nodes)
+  //   w^k  = BC^T ubar,  w^k[m] = sum_q bct_f[m][q] ubar[bct_src[m][q]]
+  //   v'   = c dt (chi0 w^k + chi1 L1 + chi2 L2 + chi3 L3)
+  // and writes v' to U and w^k to L3 (src_step = k).
+  const int* bct_src;               // [8][M][4]: tables of faces 0..3, corners 4..7
+  const float* bct_f;               // [8][M][4]
+  const float* ebar;                // [G][ebar_len][ring]: dt sum_d Wd[d][node] r[d][k]
+  int ebar_len;
 };
 
 struct StepArgs {
@@ -122,15 +135,17 @@ cudaError_t launch_objective(const double* curves64, const float* measured, size
                              double dt, float* resid, double* partial, double* J_dev,
                              cudaStream_t s, long long* launches);
 
-// rho[g][s][node] = sum_d Wn[d][node] resid[g][d][s].
+// rho[g][s][node] = scale * sum_d Wn[d][node] resid[g][d][s].
 cudaError_t launch_rho(const float* resid, const float* Wn, int n_det, int ring_len,
-                       int n_steps, int G, float* rho, cudaStream_t s, long long* launches);
+                       int n_steps, int G, float scale, float* rho, cudaStream_t s,
+                       long long* launches);
 
 // grad_a[c] -= k sum_g sum_m lambda_m u_m; grad_b[c] -= k sum_g sum_m
-// lambda_m (u - P u)_m, with lambda_m = mu_{m + M/2}, k = dtheta dt area[c].
+// lambda_m (u - P u)_m, with k = scale * area[c] (scale alone when area is
+// null) and lambda_m = mu_{m + M/2} when flip is set, mu_m otherwise.
 cudaError_t launch_grad(const float* MU, const float* Useg, const float* PT, const float* area,
                         int nx, int ny, int M, int G, size_t plane, size_t useg_group_stride,
-                        double scale, double* grad_a, double* grad_b, cudaStream_t s,
+                        double scale, int flip, double* grad_a, double* grad_b, cudaStream_t s,
                         long long* launches);
 
 cudaError_t launch_to_float(const double* in, float* out, size_t n, cudaStream_t s,

@@ -277,6 +277,32 @@ void boundary_tables(int M, double n_in, double n_out, BoundaryTables& bt) {
     }
 }
 
+bool bc_transpose_tables(const BoundaryTables& bt, int M, std::vector<int>& src, std::vector<double>& f) {
+  src.assign(static_cast<size_t>(8) * M * 4, 0);
+  f.assign(static_cast<size_t>(8) * M * 4, 0.0);
+  for (int tb = 0; tb < 8; ++tb) {
+    const bool face = tb < 4;
+    const int base = (face ? tb : tb - 4) * M;
+    const std::vector<int>& refl = face ? bt.face_refl : bt.corner_refl;
+    const std::vector<double>& fc = face ? bt.face_f : bt.corner_f;
+    const std::vector<unsigned char>& act = face ? bt.face_act : bt.corner_act;
+    for (int k = 0; k < M; ++k) {
+      const size_t e = (static_cast<size_t>(tb) * M + k) * 4;
+      for (int q = 0; q < 4; ++q) src[e + q] = k;
+      f[e] = act[base + k] ? 0.0 : 1.0;
+      int used = 1;
+      for (int m = 0; m < M; ++m) {
+        if (!act[base + m] || refl[base + m] != k) continue;
+        if (used == 4) return false;
+        src[e + used] = m;
+        f[e + used] = fc[base + m];
+        ++used;
+      }
+    }
+  }
+  return true;
+}
+
 void ring_geometry(int nx, int ny, double xmin, double xmax, double ymin, double ymax,
                    std::vector<double>& px, std::vector<double>& py,
                    std::vector<double>& weight) {

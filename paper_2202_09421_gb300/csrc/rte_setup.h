@@ -72,6 +72,15 @@ struct BoundaryTables {
 };
 void boundary_tables(int M, double n_in, double n_out, BoundaryTables& bt);
 
+// Transpose of the linear part of the boundary map (the source term is a
+// constant): on a node of table tb (faces 0..3, corners 4..7 of bt),
+// w[k] = sum_{q < 4} f[(tb M + k) 4 + q] ubar[src[(tb M + k) 4 + q]], with
+// slot 0 the node's own value (kept where k is not imposed) and slots 1..3
+// the imposed ordinates m whose reflection is k, weighted by their Fresnel
+// coefficient; unused slots have f = 0.  Returns false if some k is the
+// reflection of more than three imposed ordinates.
+bool bc_transpose_tables(const BoundaryTables& bt, int M, std::vector<int>& src, std::vector<double>& f);
+
 // Ring of boundary nodes: face 0 nodes j = 0..ny-1, then face 1 (j), face 2
 // (i = 0..nx-1), face 3 (i); node positions and trapezoid weights.
 void ring_geometry(int nx, int ny, double xmin, double xmax, double ymin, double ymax,

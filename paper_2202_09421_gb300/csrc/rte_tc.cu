@@ -22,6 +22,10 @@
 // y-pass: acc = -eta_m D_y u; the epilogue forms L = R + acc, the AB4 update
 // (eq. RTEAB4), the Fresnel boundary condition with beam or adjoint
 // injection (eq. RTE), the exitance ring (eq. OpMed), and updates u in place.
+// Transposed step of the exact discrete adjoint (BoundaryArgs::bct_src set,
+// operator images of D_x^T and D_y^T): the y-pass epilogue forms
+// ubar = w^{k+1} + R + acc (+ the readout transpose on ring nodes), the
+// transposed boundary map w^k = BC^T ubar and v = c dt sum_i chi_i w^{k+i}.
 //
 // Precision: kind::tf32 or kind::f16 (BF16 operands) with split operands.
 // Every operand x is split as hi = r(x), lo = r(x - hi), r the rounding to
@@ -528,15 +532,47 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
           const float4 q4 = *reinterpret_cast<const float4*>(buf + (3 * 16 + t) * kNC + c);
           const float4 s4 = *reinterpret_cast<const float4*>(buf + (4 * 16 + t) * kNC + c);
           const float4 ac = *reinterpret_cast<const float4*>(acc_s + t * kNC + c);
+          const size_t gidx = goff + (static_cast<size_t>(j) * nx + t0) * M + c;
+          const bool bnd = i == 0 || i == nx - 1 || j == 0 || j == ny - 1;
+          if (b.bct_src) {
+            // ubar = w^{k+1} + L^T v; the boundary finish adds the readout
+            // transpose and applies BC^T across the node's ordinates
+            float ub[4] = {r4.x + ac.x + p4.x, r4.y + ac.y + p4.y, r4.z + ac.z + p4.z, r4.w + ac.w + p4.w};
+            if (bnd) {
+              const int m0 = c - w * M;
+              const float* eb = b.ebar + (static_cast<size_t>(g) * b.ebar_len + src_step) * ring_len;
+              if (i == 0 || i == nx - 1) {
+                const float e = __ldg(eb + (i == 0 ? j : ny + j));
+                const float* wx = bc_wexit + (i == 0 ? 0 : 1) * M + m0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) ub[q] = fmaf(wx[q], e, ub[q]);
+              }
+              if (j == 0 || j == ny - 1) {
+                const float e = __ldg(eb + (j == 0 ? 2 * ny + i : 2 * ny + nx + i));
+                const float* wy = bc_wexit + (j == 0 ? 2 : 3) * M + m0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) ub[q] = fmaf(wy[q], e, ub[q]);
+              }
+              *reinterpret_cast<float4*>(un_s + t * kNC + c) = make_float4(ub[0], ub[1], ub[2], ub[3]);
+            } else {
+              const float4 wn = make_float4(ub[0], ub[1], ub[2], ub[3]);
+              float4 v;
+              v.x = a.cdt * (kAB0 * wn.x + kAB1 * p4.x + kAB2 * q4.x + kAB3 * s4.x);
+              v.y = a.cdt * (kAB0 * wn.y + kAB1 * p4.y + kAB2 * q4.y + kAB3 * s4.y);
+              v.z = a.cdt * (kAB0 * wn.z + kAB1 * p4.z + kAB2 * q4.z + kAB3 * s4.z);
+              v.w = a.cdt * (kAB0 * wn.w + kAB1 * p4.w + kAB2 * q4.w + kAB3 * s4.w);
+              *reinterpret_cast<float4*>(L3 + gidx) = wn;
+              st_hint(U + gidx, v, pol_keep);
+            }
+            continue;
+          }
           float4 lk, un;
           lk.x = r4.x + ac.x; lk.y = r4.y + ac.y; lk.z = r4.z + ac.z; lk.w = r4.w + ac.w;
           un.x = fmaf(a.cdt, kAB0 * lk.x + kAB1 * p4.x + kAB2 * q4.x + kAB3 * s4.x, u4.x);
           un.y = fmaf(a.cdt, kAB0 * lk.y + kAB1 * p4.y + kAB2 * q4.y + kAB3 * s4.y, u4.y);
           un.z = fmaf(a.cdt, kAB0 * lk.z + kAB1 * p4.z + kAB2 * q4.z + kAB3 * s4.z, u4.z);
           un.w = fmaf(a.cdt, kAB0 * lk.w + kAB1 * p4.w + kAB2 * q4.w + kAB3 * s4.w, u4.w);
-          const size_t gidx = goff + (static_cast<size_t>(j) * nx + t0) * M + c;
           *reinterpret_cast<float4*>(L3 + gidx) = lk;
-          const bool bnd = i == 0 || i == nx - 1 || j == 0 || j == ny - 1;
           if (chunk_bnd) *reinterpret_cast<float4*>(un_s + t * kNC + c) = un;
           if (!bnd) st_hint(U + gidx, un, pol_keep);   // u^{k+1} is read by the next x-pass
         }
@@ -573,6 +609,21 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
           if ((lf || rt) && (bt || tp)) tb = 4 + (rt ? 1 : 0) + (tp ? 2 : 0);
           else tb = lf ? 0 : rt ? 1 : bt ? 2 : 3;
           const float* pre = un_s + t * kNC + w * M;
+          if (b.bct_src) {
+            // transposed step: w^k = BC^T ubar, v = c dt sum_i chi_i w^{k+i}
+            const int* src = b.bct_src + (tb * M + m) * 4;
+            const float* cf = b.bct_f + (tb * M + m) * 4;
+            float wv = 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) wv = fmaf(__ldg(cf + q), pre[__ldg(src + q)], wv);
+            const int col = w * M + m;
+            const float w1 = buf[(2 * 16 + t) * kNC + col], w2 = buf[(3 * 16 + t) * kNC + col],
+                        w3 = buf[(4 * 16 + t) * kNC + col];
+            const size_t gi = goff + (static_cast<size_t>(j) * nx + i) * M + m;
+            L3[gi] = wv;
+            U[gi] = a.cdt * (kAB0 * wv + kAB1 * w1 + kAB2 * w2 + kAB3 * w3);
+            continue;
+          }
           float val = pre[m];
           if (bc_act[tb * M + m]) {
             const int node = lf ? j : rt ? ny + j : bt ? 2 * ny + i : 2 * ny + nx + i;
@@ -793,8 +844,9 @@ cudaError_t launch_step_tc(const StepArgs& a, const BoundaryArgs& b, float* U, f
   const int ring_step = b.ring_out ? step : -1;
   cudaError_t e;
   if (ev) cudaEventRecord(ev[0], s);
-  const bool ws = a.x_variant == 0 && tc_ws_supported(a);
-  const bool pipe = a.x_variant == 2 && tc_pipe_supported(a);
+  // the transposed step exists in the one-tile-per-CTA passes only
+  const bool ws = a.x_variant == 0 && tc_ws_supported(a) && !b.bct_src;
+  const bool pipe = a.x_variant == 2 && tc_pipe_supported(a) && !b.bct_src;
   e = ws ? launch_pass_ws(true, a, b, U, R, L1, L2, L3, step, ring_step, s)
          : launch_mode<true>(a, b, U, R, L1, L2, L3, step, ring_step, s);
   if (e != cudaSuccess) return e;

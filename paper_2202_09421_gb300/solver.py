@@ -59,6 +59,15 @@ class FCDOMSolver:
         J = B.rte_adjoint_gradient(self.ctx, detectors, measured.contiguous(), ga, gb)
         return J, ga, gb
 
+    def discrete_adjoint_gradient(self, detectors, measured):
+        """J and its exact gradient with respect to the nodal a and b of the
+        discrete march (the reverse sweep with the transposed operators)."""
+        g = self.grid
+        ga = torch.empty((g.ny, g.nx), device=self.device, dtype=torch.float32)
+        gb = torch.empty_like(ga)
+        J = B.rte_discrete_adjoint_gradient(self.ctx, detectors, measured.contiguous(), ga, gb)
+        return J, ga, gb
+
     def state(self, group: int) -> torch.Tensor:
         g = self.grid
         out = torch.empty((g.ny, g.nx, g.M), device=self.device, dtype=torch.float32)
