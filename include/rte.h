@@ -278,16 +278,26 @@ long long rte_kernel_launches(const rte_ctx* ctx);
 /* Number of CUDA graphs captured by this context (RTE_FLAG_CUDA_GRAPH). */
 long long rte_graph_captures(const rte_ctx* ctx);
 
-/* Kernel schedule of the tensor-core precisions (no counterpart in the
- * paper; a scheduling choice with the same arithmetic up to FP32
- * contraction order):
+/* Kernel schedule (no counterpart in the paper; a scheduling choice with
+ * the same discrete operator, up to FP32 rounding and contraction order):
  *   0  persistent warp-specialised x- and y-passes, one CTA per SM, where
- *      supported (nx, ny <= 256, M in {16, 32}, no RTE_FLAG_TC_SCATTER);
+ *      supported (tensor-core precisions; nx, ny <= 256, M in {16, 32}, no
+ *      RTE_FLAG_TC_SCATTER);
  *   1  (default) one-tile-per-CTA passes;
  *   2  one-tile-per-CTA x-pass and the pipelined persistent y-pass (the main
  *      loop of one tile and the epilogue of the previous one on two warp
- *      groups of one CTA per SM) where supported (ny <= 256).
- * Unsupported sizes run the one-tile-per-CTA passes.  Errors: INVALID_ARG. */
+ *      groups of one CTA per SM) where supported (tensor-core precisions,
+ *      ny <= 256);
+ *   3  tile-local fused step of the decomposed operator (Sec. 4.4,
+ *      Algorithm 1): one launch per step, one CTA per subdomain and group,
+ *      the whole step (segment derivatives, scattering, AB4, boundary
+ *      condition, exitance) in shared memory with FP32 arithmetic, in every
+ *      precision; where supported (fc_parts_x, fc_parts_y >= 2 with owned
+ *      ranges of at most 16 points, M in {16, 32}) by rte_forward and
+ *      rte_adjoint_gradient (rte_discrete_adjoint_gradient and the batched
+ *      and allocation-free forwards run the one-tile-per-CTA passes).
+ * Unsupported sizes run the one-tile-per-CTA passes (the plain FP32 passes
+ * in RTE_PREC_FP32).  Errors: INVALID_ARG. */
 rte_status rte_set_pass_variant(rte_ctx* ctx, int variant);
 
 /* Autotuner (no counterpart in the paper): times every kernel configuration

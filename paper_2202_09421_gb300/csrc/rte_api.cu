@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "../../include/rte.h"
@@ -37,6 +38,11 @@ struct rte_ctx {
   // exact discrete adjoint (built on its first use)
   DevBuf DxTt, DyTt, DxImgT, DyImgT, bct_src, bct_f;
   bool transposed_ready = false;
+  // tile-local fused step (decomposed operators): per-part ranges and the
+  // packed segment operators of each axis
+  DevBuf fxp, fyp, FxT, FyT;
+  int fused_own_max = 0;
+  bool fused_exact = true;          // every part owns kFusedOwnMax points
   int tc_mode = 0;                 // the precision: 0 SIMT FP32, 1-4 tcgen05 forms
   int x_variant = 1;               // pass kernels: 0 persistent warp-specialised, 1 one tile per CTA, 2 pipelined y-pass
   // state of the last forward
@@ -161,6 +167,14 @@ rte_kern::StepArgs step_args(rte_ctx* c, int G) {
   a.DxImg = c->DxImg.p;
   a.DyImg = c->DyImg.p;
   a.PImg = F(c->PImg);
+  a.px = c->par.fc_parts_x;
+  a.py = c->par.fc_parts_y;
+  a.fxp = static_cast<const int*>(c->fxp.p);
+  a.fyp = static_cast<const int*>(c->fyp.p);
+  a.FxT = F(c->FxT);
+  a.FyT = F(c->FyT);
+  a.fused_own_max = c->fused_own_max;
+  a.fused_exact = c->fused_exact ? 1 : 0;
   return a;
 }
 
@@ -226,13 +240,18 @@ rte_status march(rte_ctx* c, DevBuf& U, DevBuf& R, DevBuf* L, int& hl, int G, in
   const rte_kern::StepArgs a = step_args(c, G);
   const size_t gbytes = static_cast<size_t>(G) * c->plane * sizeof(float);
   const int I = c->par.ckpt_interval;
+  // The tile-local fused step reads u^k from one buffer and writes u^{k+1}
+  // to the other (R, which it does not otherwise use); the state ends in U.
+  const bool fused = a.x_variant == 3 && rte_kern::fused_supported(a);
+  float* cur = F(U);
+  float* oth = F(R);
   for (int s = s_begin; s < s_end; ++s) {
     float* L1 = F(L[hl]);
     float* L2 = F(L[(hl + 1) % 3]);
     float* L3 = F(L[(hl + 2) % 3]);
     if (save_ckpt && I > 0 && s % I == 0) {
       char* base = static_cast<char*>(c->ckpt.p) + static_cast<size_t>(s / I) * 4 * gbytes;
-      const void* src[4] = {U.p, L1, L2, L3};
+      const void* src[4] = {cur, L1, L2, L3};
       for (int q = 0; q < 4; ++q)
         RTE_TRY(cuda_status(cudaMemcpyAsync(base + q * gbytes, src[q], gbytes,
                                             cudaMemcpyDeviceToDevice, c->stream)));
@@ -246,22 +265,30 @@ rte_status march(rte_ctx* c, DevBuf& U, DevBuf& R, DevBuf* L, int& hl, int G, in
       }
       ev = &c->events[3 * c->n_timed++];
     }
-    RTE_TRY(cuda_status(rte_kern::launch_step(a, b, F(U), F(R), L1, L2, L3, s, c->stream,
-                                              &c->launches, ev)));
+    if (fused) {
+      RTE_TRY(cuda_status(rte_kern::launch_step_fused(a, b, cur, oth, L1, L2, L3, s, c->stream,
+                                                      &c->launches, ev)));
+      std::swap(cur, oth);
+    } else {
+      RTE_TRY(cuda_status(rte_kern::launch_step(a, b, cur, F(R), L1, L2, L3, s, c->stream,
+                                                &c->launches, ev)));
+    }
     hl = (hl + 2) % 3;
     if (fluence_out && snap_index[s] >= 0) {
       const size_t per = static_cast<size_t>(c->nx) * c->ny;
       const int n_snaps = static_cast<int>(std::count_if(snap_index.begin(), snap_index.end(),
                                                          [](int v) { return v >= 0; }));
       RTE_TRY(cuda_status(rte_kern::launch_fluence(
-          F(U), fluence_out + static_cast<size_t>(snap_index[s]) * per, per * n_snaps, c->nx,
+          cur, fluence_out + static_cast<size_t>(snap_index[s]) * per, per * n_snaps, c->nx,
           c->ny, c->M, G, c->plane, static_cast<float>(2.0 * kPi / c->M), c->stream,
           &c->launches)));
     }
     if (seg_out)
-      RTE_TRY(cuda_status(cudaMemcpyAsync((*seg_out)[s - s_begin], U.p, gbytes,
+      RTE_TRY(cuda_status(cudaMemcpyAsync((*seg_out)[s - s_begin], cur, gbytes,
                                           cudaMemcpyDeviceToDevice, c->stream)));
   }
+  if (cur != F(U))
+    RTE_TRY(cuda_status(cudaMemcpyAsync(U.p, cur, gbytes, cudaMemcpyDeviceToDevice, c->stream)));
   return RTE_OK;
 }
 
@@ -503,7 +530,7 @@ const char* rte_last_cuda_error(void) { return cudaGetErrorName(g_last_cuda_erro
 long long rte_graph_captures(const rte_ctx* ctx) { return ctx ? ctx->graph_captures : -1; }
 
 rte_status rte_set_pass_variant(rte_ctx* c, int variant) {
-  if (!c || variant < 0 || variant > 2) return RTE_ERR_INVALID_ARG;
+  if (!c || variant < 0 || variant > 3) return RTE_ERR_INVALID_ARG;
   c->x_variant = variant;
   return RTE_OK;
 }
@@ -626,7 +653,7 @@ rte_status rte_destroy(rte_ctx* c) {
                    &c->LA[1], &c->LA[2], &c->seg, &c->curves64, &c->resid, &c->partial,
                    &c->Jdev, &c->rho, &c->grad_a, &c->grad_b, &c->Wd, &c->Wn, &c->lohi,
                    &c->DxImg, &c->DyImg, &c->PImg, &c->DxTt, &c->DyTt, &c->DxImgT, &c->DyImgT,
-                   &c->bct_src, &c->bct_f};
+                   &c->bct_src, &c->bct_f, &c->fxp, &c->fyp, &c->FxT, &c->FyT};
   for (DevBuf* b : all) release(*b);
   release(c->batch_tab);
   for (cudaEvent_t e : c->events) cudaEventDestroy(e);
@@ -691,11 +718,41 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
   const double hs[2] = {c->dx, c->dy};
   const int parts[2] = {p->fc_parts_x, p->fc_parts_y};
   DevBuf* dst[2] = {&c->DxT, &c->DyT};
+  std::vector<int> part_tab[2];
+  std::vector<float> seg_ops[2];
   for (int ax = 0; ax < 2; ++ax) {
     const int n = dims[ax];
     if (!rte_setup::fc_derivative_matrix_parts(n, hs[ax], p->filter_alpha, p->filter_beta, parts[ax], Dm))
       return fail(RTE_ERR_INVALID_ARG);
     const rte_status s = upload_operator(c, Dm, n, *dst[ax], ax == 0 ? c->DxImg : c->DyImg);
+    if (s != RTE_OK) return fail(s);
+    // Tile-local fused step: each part's owned rows of its segment
+    // operator, transposed and zero-padded to [kFusedOwnMax + 4][kFusedOwnMax].
+    if (parts[ax] >= 2) {
+      constexpr int kO = rte_kern::kFusedOwnMax, kS = kO + 4;
+      part_tab[ax].assign(4 * parts[ax], 0);
+      seg_ops[ax].assign(static_cast<size_t>(parts[ax]) * kS * kO, 0.f);
+      for (int k = 0; k < parts[ax]; ++k) {
+        int lo, hi, slo, shi;
+        rte_setup::part_range(n, parts[ax], k, lo, hi, slo, shi);
+        const int* v[4] = {&lo, &hi, &slo, &shi};
+        for (int q = 0; q < 4; ++q) part_tab[ax][4 * k + q] = *v[q];
+        c->fused_own_max = std::max(c->fused_own_max, hi - lo);
+        if (hi - lo != rte_kern::kFusedOwnMax) c->fused_exact = false;
+        if (hi - lo > kO) continue;   // the fused step is then unsupported
+        for (int kk = 0; kk < shi - slo; ++kk)
+          for (int i = 0; i < hi - lo; ++i)
+            seg_ops[ax][(static_cast<size_t>(k) * kS + kk) * kO + i] =
+                static_cast<float>(Dm[static_cast<size_t>(lo + i) * n + slo + kk]);
+      }
+    }
+  }
+  if (parts[0] >= 2 && parts[1] >= 2) {
+    rte_status s = upload(c->fxp, part_tab[0], c->stream);
+    if (s == RTE_OK) s = upload(c->fyp, part_tab[1], c->stream);
+    if (s == RTE_OK) s = upload(c->FxT, seg_ops[0], c->stream);
+    if (s == RTE_OK) s = upload(c->FyT, seg_ops[1], c->stream);
+    if (s == RTE_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
     if (s != RTE_OK) return fail(s);
   }
   c->rho_dx = rte_setup::fc_spectral_radius_parts(g->nx, c->dx, p->filter_alpha, p->filter_beta, p->fc_parts_x);
@@ -973,6 +1030,11 @@ static rte_status adjoint_impl(rte_ctx* c, const rte_detector* dets, int n_det, 
     ba.rho = F(c->rho); ba.rho_len = N;
   }
   const double scale = (2.0 * kPi / c->M) * c->par.dt;
+  // continuous form with the tile-local fused step: MU and RA alternate as
+  // input and output state
+  const bool fused_adj = !discrete && sa.x_variant == 3 && rte_kern::fused_supported(sa);
+  float* mcur = F(c->MU);
+  float* moth = F(c->RA);
   int hl_adj = 0;
   std::vector<int> no_snaps(N, -1);
   // Levels needed: forward steps 0 .. N-2 (the adjoint vanishes at the last).
@@ -1046,12 +1108,17 @@ static rte_status adjoint_impl(rte_ctx* c, const rte_detector* dets, int n_det, 
       float* L1 = F(c->LA[hl_adj]);
       float* L2 = F(c->LA[(hl_adj + 1) % 3]);
       float* L3 = F(c->LA[(hl_adj + 2) % 3]);
-      if (!discrete) {
+      if (fused_adj) {
+        RTE_TRY(cuda_status(rte_kern::launch_step_fused(sa, ba, mcur, moth, L1, L2, L3, lvl, c->stream,
+                                                        &c->launches)));
+        std::swap(mcur, moth);
+        hl_adj = (hl_adj + 2) % 3;
+      } else if (!discrete) {
         RTE_TRY(cuda_status(rte_kern::launch_step(sa, ba, F(c->MU), F(c->RA), L1, L2, L3, lvl, c->stream,
                                                   &c->launches)));
         hl_adj = (hl_adj + 2) % 3;
       }
-      RTE_TRY(cuda_status(rte_kern::launch_grad(F(c->MU), segp[lvl - s0], F(c->PT),
+      RTE_TRY(cuda_status(rte_kern::launch_grad(mcur, segp[lvl - s0], F(c->PT),
                                                 discrete ? nullptr : F(c->area), c->nx, c->ny, c->M, G,
                                                 c->plane, c->plane, discrete ? 1.0 : scale, discrete ? 0 : 1,
                                                 dJ_dmua ? D(c->grad_a) : nullptr,

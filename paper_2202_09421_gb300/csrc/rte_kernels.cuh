@@ -62,7 +62,21 @@ struct StepArgs {
   const void* DxImg;
   const void* DyImg;
   const float* PImg;                // phase matrix as the scattering operand
+  // Tile-local fused step (x_variant 3) of the decomposed operator: per part
+  // {lo, hi, slo, shi} (owned range, segment) and the part's segment operator
+  // transposed and packed [part][k < kFusedOwnMax + 4][i < kFusedOwnMax]
+  // (entry (k, i): derivative at owned point lo + i from segment point slo + k).
+  int px, py;
+  const int* fxp;
+  const int* fyp;
+  const float* FxT;
+  const float* FyT;
+  int fused_own_max;                // largest owned range over both axes
+  int fused_exact;                  // every part owns exactly kFusedOwnMax points
 };
+
+// Largest owned range per axis of the tile-local fused step.
+constexpr int kFusedOwnMax = 16;
 
 // One AB4 step on all groups: x-pass (R = b P u - (a+b) u - xi d_x u), then
 // y-pass (L = R - eta d_y u, AB4 update, boundary condition, exitance).
@@ -116,6 +130,15 @@ bool tc_pipe_supported(const StepArgs& a);
 cudaError_t launch_ypass_pipe(const StepArgs& a, const BoundaryArgs& b, float* U, const float* R, const float* L1,
                               const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s);
 cudaError_t pipe_take_error(int* flag);
+
+// Tile-local fused step (rte_fused.cu): one launch per step over the
+// subdomains of the decomposed operator (parts >= 2 on both axes, owned
+// ranges <= kFusedOwnMax, M in {16, 32}); reads u^k from Uin and writes
+// u^{k+1} to Uout (different buffers).
+bool fused_supported(const StepArgs& a);
+cudaError_t launch_step_fused(const StepArgs& a, const BoundaryArgs& b, const float* Uin, float* Uout,
+                              const float* L1, const float* L2, float* L3, int step, cudaStream_t s,
+                              long long* launches, cudaEvent_t* ev = nullptr);
 
 // Phi[g][j][i] = w sum_m u_m  (eq. photondensity).
 cudaError_t launch_fluence(const float* U, float* out, size_t out_group_stride, int nx, int ny,

@@ -72,14 +72,14 @@ void fc_derivative_matrix(int n, double h, double alpha, double beta,
 namespace {
 constexpr int kFringe = 2;   // fringe points on each interior side (Sec. 4.4)
 
-// Owned range [lo, hi) and segment [slo, shi) of part k of `parts`.
+}  // namespace
+
 void part_range(int n, int parts, int k, int& lo, int& hi, int& slo, int& shi) {
   lo = static_cast<int>(static_cast<long long>(k) * n / parts);
   hi = static_cast<int>(static_cast<long long>(k + 1) * n / parts);
   slo = k > 0 ? lo - kFringe : lo;
   shi = k < parts - 1 ? hi + kFringe : hi;
 }
-}  // namespace
 
 bool fc_derivative_matrix_parts(int n, double h, double alpha, double beta, int parts,
                                 std::vector<double>& D) {

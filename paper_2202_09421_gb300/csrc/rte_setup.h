@@ -26,6 +26,9 @@ void fc_derivative_matrix(int n, double h, double alpha, double beta,
 // than 16 points.
 bool fc_derivative_matrix_parts(int n, double h, double alpha, double beta, int parts,
                                 std::vector<double>& D);
+// Owned range [lo, hi) and segment [slo, shi) of part k of `parts` (two
+// fringe points on each interior side).
+void part_range(int n, int parts, int k, int& lo, int& hi, int& slo, int& shi);
 // Largest spectral-radius estimate over the segments of a decomposition.
 double fc_spectral_radius_parts(int n, double h, double alpha, double beta, int parts);
 

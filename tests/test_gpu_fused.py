@@ -1,0 +1,135 @@
+"""GPU parity of the tile-local fused step (rte_set_pass_variant 3: one
+kernel per step over the subdomains of Sec. 4.4 / Algorithm 1, FP32) against
+the oracle with the same decomposition, and against the two-pass kernels
+applying the same decomposed operator; its checkpointed adjoint, CUDA-graph
+replay and the fallback when the decomposition does not admit it."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import rel_l2
+from oracle.rte import Solver
+from rte_inputs import workload_custom
+
+pytestmark = pytest.mark.gpu
+
+FUSED = 3
+
+
+def _solver(wl, parts, precision=0, ckpt=0, flags=0, variant=FUSED):
+    from paper_2202_09421_gb300 import binding as B
+    from paper_2202_09421_gb300.solver import FCDOMSolver
+    dev = torch.device("cuda:0")
+    s = FCDOMSolver(wl.grid, wl.optics, torch.tensor(wl.mua, dtype=torch.float32, device=dev),
+                    torch.tensor(wl.mus, dtype=torch.float32, device=dev), wl.c, wl.dt, precision=precision,
+                    fc_parts=parts, ckpt_interval=ckpt, flags=flags)
+    B.rte_set_pass_variant(s.ctx, variant)
+    return s
+
+
+def _run(s, wl):
+    fl = s.forward(wl.groups, wl.n_steps, list(wl.snap_steps))
+    curves = s.readout(wl.detectors).cpu().numpy()
+    states = np.stack([s.state(g).cpu().numpy() for g in range(len(wl.groups))])
+    return fl.cpu().numpy(), curves, states
+
+
+# (nx, ny, M, parts): owned ranges of 14..16 points, segments of 16..20;
+# ragged partitions (46 = 15 + 15 + 16, 45 = 15 x 3) and both kernel forms.
+CASES = [(48, 46, 16, (3, 3)), (64, 64, 32, (4, 4)), (45, 62, 32, (3, 4))]
+
+
+@pytest.mark.parametrize("nx,ny,M,parts", CASES)
+def test_fused_step_matches_oracle(nx, ny, M, parts):
+    wl = workload_custom(nx, ny, M, 120, 0.04, L=(nx - 1) / 66, mus=20.0, n_groups=2, t_s=1.0, sigma_t=0.4)
+    s = _solver(wl, parts)
+    launches0 = s.kernel_launches()
+    fl, curves, states = _run(s, wl)
+    launches = s.kernel_launches() - launches0
+    s.close()
+    S = Solver(wl, fc_parts=parts)
+    outs = [S.forward(g, wl.n_steps, wl.detectors, snap_steps=list(wl.snap_steps)) for g in wl.groups]
+    c_ref = np.stack([o["curves"] for o in outs])
+    f_ref = np.stack([[o["fluence"][k] for k in wl.snap_steps] for o in outs])
+    u_ref = np.stack([np.moveaxis(o["u"], 0, -1) for o in outs])       # [g][j][i][m]
+    ec, ef, eu = rel_l2(curves, c_ref), rel_l2(fl, f_ref), rel_l2(states, u_ref)
+    print(f"fused {nx}x{ny} M{M} parts {parts}: curves {ec:.2e}, fluence {ef:.2e}, state {eu:.2e}; "
+          f"{launches} launches")
+    assert ec <= 1e-5 and ef <= 1e-5 and eu <= 1e-5
+    # one kernel per step (plus fluence snapshots and the readout)
+    assert launches <= wl.n_steps + len(wl.snap_steps) + 2
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fused_step_matches_two_pass_decomposed(precision):
+    """Same decomposed operator through the two-pass kernels (FP32 SIMT or
+    3xTF32): the fused step agrees to FP32 rounding."""
+    wl = workload_custom(64, 64, 32, 150, 0.04, L=63 / 66, mus=20.0, n_groups=2, t_s=1.0, sigma_t=0.4)
+    s = _solver(wl, (4, 4), precision=precision)
+    _, c_f, u_f = _run(s, wl)
+    s.close()
+    s = _solver(wl, (4, 4), precision=precision, variant=1)
+    _, c_2, u_2 = _run(s, wl)
+    s.close()
+    print(f"prec {precision}: fused vs two-pass curves {rel_l2(c_f, c_2):.2e}, state {rel_l2(u_f, u_2):.2e}")
+    assert rel_l2(c_f, c_2) <= 2e-6 and rel_l2(u_f, u_2) <= 2e-6
+
+
+def test_fused_adjoint_gradient():
+    """Checkpointed continuous adjoint with the fused step (recompute and
+    adjoint march both fused) against the two-pass form of the same
+    decomposed operator and against the oracle."""
+    wl = workload_custom(48, 46, 16, 100, 0.04, L=47 / 66, mus=20.0, n_groups=2, t_s=1.0, sigma_t=0.4)
+    tgt = workload_custom(48, 46, 16, 100, 0.04, L=47 / 66, mus=20.0, n_groups=2, t_s=1.0, sigma_t=0.4,
+                          seed=7)
+    meas = np.stack([Solver(tgt, fc_parts=(3, 3)).forward(g, 100, tgt.detectors)["curves"]
+                     for g in tgt.groups]) * 0.8
+    res = {}
+    for variant in (FUSED, 1):
+        s = _solver(wl, (3, 3), ckpt=13, variant=variant)
+        s.forward(wl.groups, wl.n_steps)
+        m = torch.tensor(meas, dtype=torch.float32, device=s.device)
+        res[variant] = s.adjoint_gradient(wl.detectors, m)
+        s.close()
+    S = Solver(wl, fc_parts=(3, 3))
+    Jo, gao = 0.0, 0.0
+    for k, g in enumerate(wl.groups):
+        j, a_, _, _ = S.adjoint_gradient(g, wl.n_steps, wl.detectors, meas[k])
+        Jo, gao = Jo + j, gao + a_
+    Jf, gaf, gbf = res[FUSED]
+    J2, ga2, gb2 = res[1]
+    print(f"fused adjoint: J {Jf:.6e} / {J2:.6e} / oracle {Jo:.6e}; grad_a vs two-pass "
+          f"{rel_l2(gaf.cpu(), ga2.cpu()):.2e}, vs oracle {rel_l2(gaf.cpu(), gao):.2e}")
+    assert abs(Jf - Jo) < 1e-5 * abs(Jo)
+    assert rel_l2(gaf.cpu(), ga2.cpu()) < 1e-5 and rel_l2(gbf.cpu(), gb2.cpu()) < 1e-5
+    assert rel_l2(gaf.cpu(), gao) < 1e-4
+
+
+def test_fused_graph_replay_and_fallback():
+    """CUDA-graph replay of the fused march equals the direct launches bit
+    for bit (an odd step count leaves the state in the second buffer); a
+    decomposition the fused step does not admit (owned ranges above 16)
+    runs the two-pass kernels."""
+    from paper_2202_09421_gb300 import binding as B
+    wl = workload_custom(48, 46, 16, 37, 0.04, L=47 / 66, mus=20.0, n_groups=1, t_s=1.0, sigma_t=0.4)
+    s = _solver(wl, (3, 3))
+    _, c0, u0 = _run(s, wl)
+    s.close()
+    s = _solver(wl, (3, 3), flags=B.RTE_FLAG_CUDA_GRAPH)
+    _run(s, wl)
+    _, c1, u1 = _run(s, wl)
+    assert s.graph_captures() == 1
+    s.close()
+    assert np.array_equal(c0, c1) and np.array_equal(u0, u1)
+    # 48 / 2 = 24-point owned ranges: not admitted, same result as variant 1
+    s = _solver(wl, (2, 2))
+    n0 = s.kernel_launches()
+    s.forward(wl.groups, wl.n_steps)
+    assert s.kernel_launches() - n0 == 2 * wl.n_steps
+    u_a = s.state(0).cpu().numpy()
+    s.close()
+    s = _solver(wl, (2, 2), variant=1)
+    s.forward(wl.groups, wl.n_steps)
+    u_b = s.state(0).cpu().numpy()
+    s.close()
+    assert np.array_equal(u_a, u_b)
