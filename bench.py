@@ -53,21 +53,19 @@ def load_peaks():
 PEAKS = load_peaks()
 
 # DRAM traffic per launch from an ncu capture, valid only for the kernel
-# source it was taken on (sha256 of csrc/rte_kernels.cu, first 16 hex digits).
+# source it was taken on.
 NCU_TRAFFIC = {
-    # ncu --set full on the tomography workload's per-launch size (16 groups x
-    # 256^2 x 32).  Plain FP32 SIMT passes (csrc/rte_kernels.cu):
-    # profiles/fcdom_passes_tomo256_ncu_full.md
-    ("xpass_kernel", "7ec20f8a420c3adc"): 136.062464e6 + 86.956800e6,
-    ("ypass_kernel", "7ec20f8a420c3adc"): 672.236800e6 + 234.185472e6,
+    # dram__bytes_read.sum + dram__bytes_write.sum of one launch from ncu --set
+    # full on the tomography workload's per-launch size (16 groups x 256^2 x
+    # 32), keyed by the kernel and the sha256 prefix of its sources; an entry
+    # whose sources changed since its capture no longer matches.
     # tcgen05 3xTF32 passes, one tile per CTA (csrc/rte_tc.cu + rte_tc_common.cuh):
     # profiles/tc_passes_tomo256_ncu_full.md
-    ("tc_pass_kernel<x>", "4f36e1185847c61d"): 136.543744e6 + 82.921984e6,
-    ("tc_pass_kernel<y>", "4f36e1185847c61d"): 687.281408e6 + 192.194304e6,
-    # persistent warp-specialised passes (csrc/rte_tc_ws.cu + rte_tc_common.cuh):
-    # profiles/tc_pass_ws_tomo256_ncu_full.md
-    ("tc_pass_ws<x>", "ff308bb1883a1817"): 135.533568e6 + 83.505152e6,
-    ("tc_pass_ws<y>", "ff308bb1883a1817"): 794.347520e6 + 235.415040e6,
+    ("tc_pass_kernel<x>", "855a828dbd9638c2"): 136.838144e6 + 83.234816e6,
+    ("tc_pass_kernel<y>", "855a828dbd9638c2"): 687.241728e6 + 192.933632e6,
+    # tile-local fused step, 16 x 16 parts (csrc/rte_fused.cu):
+    # profiles/fused_step_tomo256_ncu_full.md
+    ("fused_step_kernel", "58329b60ffd7ff3f"): 538.784256e6 + 231.106560e6,
 }
 
 
@@ -79,6 +77,8 @@ def kernel_source_hash(name="tc_pass_ws"):
         srcs = ["rte_tc_pipe.cu", "rte_tc_common.cuh"]
     elif name.startswith("tc_pass"):
         srcs = ["rte_tc.cu", "rte_tc_common.cuh"]
+    elif name.startswith("fused_step"):
+        srcs = ["rte_fused.cu"]
     else:
         srcs = ["rte_kernels.cu"]
     h = hashlib.sha256()
@@ -257,13 +257,16 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
-    def time_form(precision, steps, warmup, clocks=None, fc_parts=(1, 1)):
+    def time_form(precision, steps, warmup, clocks=None, fc_parts=(1, 1), variant=None):
         """Forward solve + detector readout per step; CUDA events on the
         launching stream; L2 flushed before every timed step."""
         solver = FCDOMSolver(g, wl.optics, a, b, wl.c, wl.dt, ckpt_interval=0, precision=precision,
                              fc_parts=fc_parts)
         schedule = "one-tile" if args.no_autotune else args.schedule
-        if precision == B.RTE_PREC_FP32:
+        if variant is not None:
+            B.rte_set_pass_variant(solver.ctx, variant)
+            tuned = (variant, {})
+        elif precision == B.RTE_PREC_FP32:
             tuned = (1, {})
         elif schedule == "auto":
             tuned = solver.autotune(wl.groups, 40)
@@ -342,6 +345,27 @@ def run_ours(args):
         ms2 = max_over_ranks(ms2)
         forms[name] = {"value": updates * world / (ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2,
                        "headline_speedup": ms2 / ms_step}
+    # The tile-local fused step (one kernel per step) of the decomposed
+    # operator with 16 x 16 parts (16-point owned ranges), FP32 arithmetic;
+    # its two-pass counterpart (same operator) beside it.  Roofline: the
+    # one-pass algorithmic 24 B per update (read u, L1..L3; write u, L).
+    s2, ms2, pm2, pc2, _, _, _ = time_form(B.RTE_PREC_FP32, 1, 1, fc_parts=(16, 16), variant=3)
+    s2.close()
+    ms2 = max_over_ranks(ms2)
+    k_ms = pm2[1] / max(1, pc2[1])
+    fused_gbs = 24.0 * ncell_m / (k_ms / 1e3) / 1e9
+    forms["tile_local_fused_16x16"] = {
+        "value": updates * world / (ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2, "headline_speedup": ms2 / ms_step,
+        "operator": "decomposed FC (Sec. 4.4), 16 x 16 parts, FP32",
+        "roofline": {"bound": "hbm", "achieved": fused_gbs, "peak": PEAKS["hbm_gbs"], "unit": "GB/s",
+                     "frac": fused_gbs / PEAKS["hbm_gbs"], "kernel": "fused_step_kernel",
+                     "ms_per_launch": k_ms,
+                     "traffic": NCU_TRAFFIC.get(("fused_step_kernel", kernel_source_hash("fused_step_kernel")))}}
+    s2, ms2, _, _, _, _, _ = time_form(B.RTE_PREC_TF32X3, 1, 1, fc_parts=(16, 16), variant=1)
+    s2.close()
+    ms2 = max_over_ranks(ms2)
+    forms["tf32x3_subdomains_16x16_two_pass"] = {"value": updates * world / (ms2 / 1e3), "unit": UNIT,
+                                                 "ms_per_step": ms2, "headline_speedup": ms2 / ms_step}
 
     # End to end through the public API with host buffers: copy the medium
     # from pinned host memory, solve, read the detector curves back.

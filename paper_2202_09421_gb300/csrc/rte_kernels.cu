@@ -142,6 +142,9 @@ __device__ inline float warp_sum(float v) {
   return v;
 }
 
+// TR: the transposed step of the discrete adjoint (BoundaryArgs::bct_src);
+// a separate instance, so that the forward step compiles without it.
+template <bool TR>
 __global__ void __launch_bounds__(512) ypass_kernel(StepArgs a, BoundaryArgs b, float* __restrict__ U,
                                                      const float* __restrict__ R,
                                                      const float* __restrict__ L1,
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(512) ypass_kernel(StepArgs a, BoundaryArgs b, 
     const float l1[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
     const float l2[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
     const float l3[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
-    if (b.bct_src) {
+    if constexpr (TR) {
       // transposed step: ubar = w^{k+1} + L^T v (readout term and BC^T below)
 #pragma unroll
       for (int t = 0; t < kTN; ++t) acc[jj][t] = rv[t] - eta[t] * acc[jj][t] + l1[t];
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(512) ypass_kernel(StepArgs a, BoundaryArgs b, 
     const bool lf = ic == 0, rt = ic == nx - 1, bt = j == 0, tp = j == n - 1;
     const bool bnd = lf || rt || bt || tp;
     float* dst = Ug + (static_cast<size_t>(j) * nx + ic) * M;
-    if (b.bct_src) {
+    if constexpr (TR) {
       // Transposed step on this node: the readout transpose on the ring
       // (every face the node lies on), w = BC^T ubar, then the transposed
       // AB4 combination v' = c dt (chi0 w + chi1 w^{k+1} + chi2 w^{k+2} + chi3 w^{k+3}).
@@ -461,7 +464,8 @@ cudaError_t launch_step(const StepArgs& a, const BoundaryArgs& b, float* U, floa
   const size_t smx = pass_smem(a.nx, a.M, true), smy = pass_smem(a.ny, a.M, false);
   if (!attr_done) {
     cudaFuncSetAttribute(xpass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-    cudaFuncSetAttribute(ypass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    cudaFuncSetAttribute(ypass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    cudaFuncSetAttribute(ypass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     attr_done = true;
   }
   const int per_tile = kTileCols / a.M;
@@ -474,7 +478,10 @@ cudaError_t launch_step(const StepArgs& a, const BoundaryArgs& b, float* U, floa
   dim3 by(kTileCols / kTN, round_up(a.ny, kRowPad) / kTM);
   dim3 gy((a.nx + per_tile - 1) / per_tile, 1, a.G);
   const int ring_step = b.ring_out ? step : -1;
-  ypass_kernel<<<gy, by, smy, s>>>(a, b, U, R, L1, L2, L3, step, ring_step);
+  if (b.bct_src)
+    ypass_kernel<true><<<gy, by, smy, s>>>(a, b, U, R, L1, L2, L3, step, ring_step);
+  else
+    ypass_kernel<false><<<gy, by, smy, s>>>(a, b, U, R, L1, L2, L3, step, ring_step);
   if (ev) cudaEventRecord(ev[2], s);
   if (launches) *launches += 2;
   return cudaGetLastError();

@@ -39,19 +39,22 @@ def relative_error(a, a_true, area) -> float:
     return float(np.sqrt(num / den))
 
 
-def gpu_evaluator(solver, groups, n_steps: int, detectors, measured, mus):
+def gpu_evaluator(solver, groups, n_steps: int, detectors, measured, mus, exact: bool = False):
     """J(a) and dJ/da for the library: set the medium (a, mus), run the
     forward march of every group, then the checkpointed adjoint march
-    (the solver needs a checkpoint interval).  a is a host [ny][nx] array."""
+    (the solver needs a checkpoint interval): the paper's continuous
+    adjoint, or with exact=True the exact gradient of the discrete objective.
+    a is a host [ny][nx] array."""
     import torch
 
     dev = solver.device
+    grad = solver.discrete_adjoint_gradient if exact else solver.adjoint_gradient
 
     def evaluate(a: np.ndarray):
         at = torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
         solver.set_medium(at, mus)
         solver.forward(groups, n_steps)
-        J, ga, _ = solver.adjoint_gradient(detectors, measured)
+        J, ga, _ = grad(detectors, measured)
         return float(J), ga.double().cpu().numpy()
 
     return evaluate

@@ -111,20 +111,23 @@ class RTEObjective(torch.autograd.Function):
     """J(mua, mus) = sum over groups of eq. (FObj) for the given beams and
     detectors.  forward: rte_forward + rte_objective; backward: the adjoint
     march of eq. (AdjointProblem) with checkpoint recompute, giving dJ/dmua
-    and dJ/dmus per grid node (eq. FDwin22)."""
+    and dJ/dmus per grid node (eq. FDwin22), or, with exact=True, the
+    exact gradient of the discrete objective (the reverse sweep of the
+    march, rte_discrete_adjoint_gradient)."""
 
     @staticmethod
-    def forward(ctx, mua, mus, measured, solver: FCDOMSolver, groups, n_steps, detectors):
+    def forward(ctx, mua, mus, measured, solver: FCDOMSolver, groups, n_steps, detectors, exact=False):
         solver.set_medium(mua.detach(), mus.detach())
         solver.forward(groups, n_steps)
         J = solver.objective(detectors, measured)
-        ctx.solver, ctx.detectors = solver, detectors
+        ctx.solver, ctx.detectors, ctx.exact = solver, detectors, exact
         ctx.save_for_backward(measured)
         return torch.tensor(J, dtype=torch.float64, device=mua.device)
 
     @staticmethod
     def backward(ctx, gJ):
         (measured,) = ctx.saved_tensors
-        _, ga, gb = ctx.solver.adjoint_gradient(ctx.detectors, measured)
+        grad = ctx.solver.discrete_adjoint_gradient if ctx.exact else ctx.solver.adjoint_gradient
+        _, ga, gb = grad(ctx.detectors, measured)
         scale = gJ.to(torch.float32)
-        return scale * ga, scale * gb, None, None, None, None, None
+        return scale * ga, scale * gb, None, None, None, None, None, None

@@ -118,3 +118,19 @@ def test_discrete_adjoint_is_the_gradient_of_the_library_objective():
     # FP32 rounding of J over the step (observed 4e-5 of the difference)
     assert abs(dd - fd) < 5e-4 * abs(fd)
     assert abs(dd - fd) < abs(dc - fd)
+
+
+def test_autograd_function_exact_backward():
+    """RTEObjective(exact=True): backward is the exact discrete gradient."""
+    from paper_2202_09421_gb300.solver import RTEObjective
+    wl, meas = _case(40, 36, 16, steps=60, groups=1)
+    s = _gpu(wl, TF32X3, 20)
+    a = torch.tensor(wl.mua, dtype=torch.float32, device=s.device, requires_grad=True)
+    b = torch.tensor(wl.mus, dtype=torch.float32, device=s.device, requires_grad=True)
+    m = torch.tensor(meas, dtype=torch.float32, device=s.device)
+    J = RTEObjective.apply(a, b, m, s, wl.groups, wl.n_steps, wl.detectors, True)
+    J.backward()
+    J2, ga, gb = s.discrete_adjoint_gradient(wl.detectors, m)
+    s.close()
+    assert abs(J.item() - J2) < 1e-12 * abs(J2)
+    assert torch.equal(a.grad, ga) and torch.equal(b.grad, gb)
