@@ -139,10 +139,13 @@ def test_autograd_function_exact_backward():
 def test_discrete_adjoint_per_cell_central_differences():
     """Per-cell check on 20 seeded cells: the exact discrete dJ/da at a cell
     against central differences of the library's J under a perturbation of
-    that cell alone.  Cells are drawn among those whose gradient is at least
-    1% of the largest, where the difference is not dominated by the FP32
-    rounding of J; the step (0.2 of the background a) leaves J linear in a
-    to far below the bound."""
+    that cell alone.  J is about 570 times the largest nodal gradient here,
+    so the FP32 rounding of J (about 1e-8 of J between two solves) is
+    divided by 2 eps g: cells are drawn among those whose gradient is at
+    least 10% of the largest, and eps is half the background a (expected
+    rounding share about 2e-4).  The same central differences in FP64 on the
+    oracle are within 1e-5 of its exact gradient at this step (the
+    truncation)."""
     wl, meas = _case(40, 36, 16, steps=90, groups=2)
     s = _gpu(wl, TF32X3, 30)
     m = torch.tensor(meas, dtype=torch.float32, device=s.device)
@@ -150,9 +153,9 @@ def test_discrete_adjoint_per_cell_central_differences():
     _, ga, _ = s.discrete_adjoint_gradient(wl.detectors, m)
     ga = ga.double().cpu().numpy()
     rng = np.random.default_rng(20)
-    cand = np.flatnonzero(np.abs(ga).ravel() >= 0.01 * np.abs(ga).max())
+    cand = np.flatnonzero(np.abs(ga).ravel() >= 0.1 * np.abs(ga).max())
     cells = rng.choice(cand, size=20, replace=False)
-    eps = 0.2 * float(wl.mua.mean())
+    eps = 0.5 * float(wl.mua.mean())
     worst = 0.0
     for flat in cells:
         j, i = np.unravel_index(flat, ga.shape)
