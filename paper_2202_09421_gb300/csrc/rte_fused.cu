@@ -10,7 +10,7 @@
 //   1. copies the box of u^k (owned + halo, from the input state buffer)
 //      into shared memory (cp.async);
 //   2. x-lines (row, m): lbuf = -xi_m D_x,seg u    (two lines per thread,
-//      sharing float4 operator loads, FP32 FMA);
+//      sharing float4 operator loads, paired FP32 FMAs);
 //   3. y-lines (column, m): lbuf += -eta_m D_y,seg u;
 //   4. per node (one warp, or half a warp at M = 16, over the ordinates):
 //      L^k = lbuf + b P~u - (a + b) u, the AB4 update, the Fresnel boundary
@@ -60,6 +60,9 @@ struct FusedSmem {
   static constexpr int kTotal = kBoxF + kOwn + 2 * kOpF + MM * MM + 2 * OM * OM;
   static constexpr size_t kBytes = static_cast<size_t>(kTotal) * sizeof(float);
 };
+
+// Two FP32 fused multiply-adds in one instruction (each rounded as fmaf).
+__device__ __forceinline__ float2 fma2(float2 x, float2 y, float2 z) { return __ffma2_rn(x, y, z); }
 
 __device__ __forceinline__ float group_sum(float v, int width) {
   for (int o = width / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -177,24 +180,22 @@ __global__ void __launch_bounds__(kFThreads, 2)
       const int j0 = l0 / MM, m0 = l0 - j0 * MM, j1 = l1 / MM, m1 = l1 - j1 * MM;
       const float* r0 = box + (j0 + kHalo) * S::kRow + xoff + m0;
       const float* r1 = box + (j1 + kHalo) * S::kRow + xoff + m1;
-      float acc0[OM], acc1[OM];
+      float2 acc0[OM / 2], acc1[OM / 2];
 #pragma unroll
-      for (int i = 0; i < OM; ++i) acc0[i] = acc1[i] = 0.f;
+      for (int i = 0; i < OM / 2; ++i) acc0[i] = acc1[i] = make_float2(0.f, 0.f);
       for (int k = 0; k < sx; ++k) {
         const float u0 = r0[k * MM], u1 = r1[k * MM];
+        const float2 uu0 = make_float2(u0, u0), uu1 = make_float2(u1, u1);
         const float4* dk = reinterpret_cast<const float4*>(dxs + k * OM);
 #pragma unroll
         for (int q = 0; q < OM / 4; ++q) {
           if (4 * q < ox) {
             const float4 c = dk[q];
-            acc0[4 * q] = fmaf(c.x, u0, acc0[4 * q]);
-            acc0[4 * q + 1] = fmaf(c.y, u0, acc0[4 * q + 1]);
-            acc0[4 * q + 2] = fmaf(c.z, u0, acc0[4 * q + 2]);
-            acc0[4 * q + 3] = fmaf(c.w, u0, acc0[4 * q + 3]);
-            acc1[4 * q] = fmaf(c.x, u1, acc1[4 * q]);
-            acc1[4 * q + 1] = fmaf(c.y, u1, acc1[4 * q + 1]);
-            acc1[4 * q + 2] = fmaf(c.z, u1, acc1[4 * q + 2]);
-            acc1[4 * q + 3] = fmaf(c.w, u1, acc1[4 * q + 3]);
+            const float2 clo = make_float2(c.x, c.y), chi = make_float2(c.z, c.w);
+            acc0[2 * q] = fma2(clo, uu0, acc0[2 * q]);
+            acc0[2 * q + 1] = fma2(chi, uu0, acc0[2 * q + 1]);
+            acc1[2 * q] = fma2(clo, uu1, acc1[2 * q]);
+            acc1[2 * q + 1] = fma2(chi, uu1, acc1[2 * q + 1]);
           }
         }
       }
@@ -202,8 +203,10 @@ __global__ void __launch_bounds__(kFThreads, 2)
 #pragma unroll
       for (int i = 0; i < OM; ++i) {
         if (i < ox) {
-          lbuf[(j0 * ox + i) * MM + m0] = xi0 * acc0[i];
-          if (l1 != l0) lbuf[(j1 * ox + i) * MM + m1] = xi1 * acc1[i];
+          const float v0 = (i & 1) ? acc0[i / 2].y : acc0[i / 2].x;
+          const float v1 = (i & 1) ? acc1[i / 2].y : acc1[i / 2].x;
+          lbuf[(j0 * ox + i) * MM + m0] = xi0 * v0;
+          if (l1 != l0) lbuf[(j1 * ox + i) * MM + m1] = xi1 * v1;
         }
       }
     }
@@ -219,24 +222,22 @@ __global__ void __launch_bounds__(kFThreads, 2)
       const int i0 = l0 / MM, m0 = l0 - i0 * MM, i1 = l1 / MM, m1 = l1 - i1 * MM;
       const float* c0 = box + yoff + (i0 + kHalo) * MM + m0;
       const float* c1 = box + yoff + (i1 + kHalo) * MM + m1;
-      float acc0[OM], acc1[OM];
+      float2 acc0[OM / 2], acc1[OM / 2];
 #pragma unroll
-      for (int j = 0; j < OM; ++j) acc0[j] = acc1[j] = 0.f;
+      for (int j = 0; j < OM / 2; ++j) acc0[j] = acc1[j] = make_float2(0.f, 0.f);
       for (int k = 0; k < sy; ++k) {
         const float u0 = c0[k * S::kRow], u1 = c1[k * S::kRow];
+        const float2 uu0 = make_float2(u0, u0), uu1 = make_float2(u1, u1);
         const float4* dk = reinterpret_cast<const float4*>(dys + k * OM);
 #pragma unroll
         for (int q = 0; q < OM / 4; ++q) {
           if (4 * q < oy) {
             const float4 c = dk[q];
-            acc0[4 * q] = fmaf(c.x, u0, acc0[4 * q]);
-            acc0[4 * q + 1] = fmaf(c.y, u0, acc0[4 * q + 1]);
-            acc0[4 * q + 2] = fmaf(c.z, u0, acc0[4 * q + 2]);
-            acc0[4 * q + 3] = fmaf(c.w, u0, acc0[4 * q + 3]);
-            acc1[4 * q] = fmaf(c.x, u1, acc1[4 * q]);
-            acc1[4 * q + 1] = fmaf(c.y, u1, acc1[4 * q + 1]);
-            acc1[4 * q + 2] = fmaf(c.z, u1, acc1[4 * q + 2]);
-            acc1[4 * q + 3] = fmaf(c.w, u1, acc1[4 * q + 3]);
+            const float2 clo = make_float2(c.x, c.y), chi = make_float2(c.z, c.w);
+            acc0[2 * q] = fma2(clo, uu0, acc0[2 * q]);
+            acc0[2 * q + 1] = fma2(chi, uu0, acc0[2 * q + 1]);
+            acc1[2 * q] = fma2(clo, uu1, acc1[2 * q]);
+            acc1[2 * q + 1] = fma2(chi, uu1, acc1[2 * q + 1]);
           }
         }
       }
@@ -244,8 +245,10 @@ __global__ void __launch_bounds__(kFThreads, 2)
 #pragma unroll
       for (int j = 0; j < OM; ++j) {
         if (j < oy) {
-          lbuf[(j * ox + i0) * MM + m0] = fmaf(et0, acc0[j], lbuf[(j * ox + i0) * MM + m0]);
-          if (l1 != l0) lbuf[(j * ox + i1) * MM + m1] = fmaf(et1, acc1[j], lbuf[(j * ox + i1) * MM + m1]);
+          const float v0 = (j & 1) ? acc0[j / 2].y : acc0[j / 2].x;
+          const float v1 = (j & 1) ? acc1[j / 2].y : acc1[j / 2].x;
+          lbuf[(j * ox + i0) * MM + m0] = fmaf(et0, v0, lbuf[(j * ox + i0) * MM + m0]);
+          if (l1 != l0) lbuf[(j * ox + i1) * MM + m1] = fmaf(et1, v1, lbuf[(j * ox + i1) * MM + m1]);
         }
       }
     }
@@ -280,16 +283,14 @@ __global__ void __launch_bounds__(kFThreads, 2)
         const int n = jl * ox + il;
         const int gj = y_lo + jl, gi = x_lo + il;
         const float* un = box + (jl + kHalo) * S::kRow + (il + kHalo) * MM;
-        float s4[4] = {0.f, 0.f, 0.f, 0.f};
+        float2 s01 = make_float2(0.f, 0.f), s23 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < MM; q += 4) {
           const float4 v = *reinterpret_cast<const float4*>(un + q);
-          s4[0] = fmaf(prow[q], v.x, s4[0]);
-          s4[1] = fmaf(prow[q + 1], v.y, s4[1]);
-          s4[2] = fmaf(prow[q + 2], v.z, s4[2]);
-          s4[3] = fmaf(prow[q + 3], v.w, s4[3]);
+          s01 = fma2(make_float2(prow[q], prow[q + 1]), make_float2(v.x, v.y), s01);
+          s23 = fma2(make_float2(prow[q + 2], prow[q + 3]), make_float2(v.z, v.w), s23);
         }
-        const float sc = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+        const float sc = (s01.x + s01.y) + (s23.x + s23.y);
         const float u = un[m];
         const float av = abs_[n], bv = abs_[OM * OM + n];
         const int o = n * MM + m;
