@@ -65,7 +65,7 @@ NCU_TRAFFIC = {
     ("tc_pass_kernel<y>", "855a828dbd9638c2"): 687.241728e6 + 192.933632e6,
     # tile-local fused step, 16 x 16 parts (csrc/rte_fused.cu):
     # profiles/fused_step_tomo256_ncu_full.md
-    ("fused_step_kernel", "58329b60ffd7ff3f"): 538.784256e6 + 231.106560e6,
+    ("fused_step_kernel", "d911f8dcf7817a68"): 538.570240e6 + 231.271168e6,
 }
 
 
