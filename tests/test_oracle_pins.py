@@ -438,3 +438,72 @@ def test_subdomain_derivative_converges():
         errs.append(np.abs(d - df).max())
     orders = [np.log(errs[k] / errs[k + 1]) / np.log((ns[k + 1] - 1) / (ns[k] - 1)) for k in range(2)]
     assert min(orders) > 3.5, (errs, orders)
+
+
+# ------------------------------------------------------------ brute force
+def test_brute_force_dense_march_on_tiny_grid():
+    """The whole scheme on a 12 x 10 grid with M = 8 as one dense linear map
+    of the (nx ny M)-vector, assembled from the definitions: eq. (RTEAB4L)
+    as Kronecker products (scattering P~ over ordinates at each node, D_x
+    along i, D_y along j, the local a, b), the boundary condition of eq.
+    (RTE) as a matrix found by geometry (incoming where theta.nu < 0, the
+    governing face at a corner the larger |theta.nu|, the y-face on a tie,
+    the reflected ordinate the one whose direction is the mirror image),
+    and AB4 (eq. RTEAB4) from zero start levels.  The oracle's per-line
+    march must agree to rounding at every step."""
+    from oracle.fcgram import fc_derivative
+    wl = workload_custom(12, 10, 8, 30, 0.04, L=11 / 66, mus=20.0, n_groups=1, t_s=0.5, sigma_t=0.3)
+    g, M = wl.grid, wl.grid.M
+    S = rte.Solver(wl)
+    ref = S.forward(wl.groups[0], wl.n_steps, keep_states=True)["states"]
+
+    nn = g.nx * g.ny
+    th = 2 * np.pi * np.arange(M) / M
+    cx, sy = np.cos(th), np.sin(th)
+    Dx = fc_derivative(np.eye(g.nx), g.dx, axis=0)          # column k: derivative of e_k
+    Dy = fc_derivative(np.eye(g.ny), g.dy, axis=0)
+    P = rte.phase_matrix(M, wl.optics.g, wl.optics.hg_exponent)
+    a_rep = np.tile(np.asarray(wl.mua, dtype=float).ravel(), M)
+    b_rep = np.tile(np.asarray(wl.mus, dtype=float).ravel(), M)
+    Lmat = (b_rep[:, None] * np.kron(P, np.eye(nn)) - np.diag(a_rep + b_rep)
+            - np.kron(np.diag(cx), np.kron(np.eye(g.ny), Dx))
+            - np.kron(np.diag(sy), np.kron(Dy, np.eye(g.nx))))
+
+    normals = {0: (-1.0, 0.0), 1: (1.0, 0.0), 2: (0.0, -1.0), 3: (0.0, 1.0)}
+    Bmat = np.eye(M * nn)
+    imposed = np.zeros(M * nn, dtype=bool)          # Gamma_-: the source enters only here
+    for j in range(g.ny):
+        for i in range(g.nx):
+            faces = [F for F, on in ((0, i == 0), (1, i == g.nx - 1), (2, j == 0), (3, j == g.ny - 1)) if on]
+            for m in range(M):
+                dots = {F: normals[F][0] * cx[m] + normals[F][1] * sy[m] for F in faces}
+                inc = [F for F in faces if dots[F] < -1e-12]
+                if not inc:
+                    continue
+                F = inc[0] if len(inc) == 1 else max(inc, key=lambda f: (abs(dots[f]) - (1e-12 if f < 2 else 0.0)))
+                # mirror the normal component of theta_m across face F
+                nu = normals[F]
+                rx, ry = cx[m] - 2 * dots[F] * nu[0], sy[m] - 2 * dots[F] * nu[1]
+                mr = int(np.argmin(np.hypot(cx - rx, sy - ry)))
+                row = m * nn + j * g.nx + i
+                imposed[row] = True
+                Bmat[row, :] = 0.0
+                Bmat[row, mr * nn + j * g.nx + i] = rte.fresnel(abs(dots[F]), wl.optics.n_in, wl.optics.n_out)
+
+    ab4 = np.array([55.0, -59.0, 37.0, -9.0]) / 24.0
+    bj, bi = S.bt.nodes_j, S.bt.nodes_i
+    u = np.zeros(M * nn)
+    hist = [np.zeros_like(u) for _ in range(3)]
+    cdt = wl.c * wl.dt
+    worst = 0.0
+    for s in range(wl.n_steps):
+        Lk = Lmat @ u
+        pre = u + cdt * (ab4[0] * Lk + ab4[1] * hist[0] + ab4[2] * hist[1] + ab4[3] * hist[2])
+        q = np.zeros((M, g.ny, g.nx))
+        q[:, bj, bi] = S.beam_inflow(wl.groups[0], (4 + s) * wl.dt).T
+        u = Bmat @ pre + np.where(imposed, q.ravel(), 0.0)
+        hist = [Lk, hist[0], hist[1]]
+        worst = max(worst, np.abs(u - ref[s].ravel()).max() / np.abs(ref[s]).max())
+    assert np.abs(ref[-1]).max() > 0
+    print(f"dense march vs oracle: {worst:.1e}")
+    assert worst < 1e-11, worst
