@@ -578,15 +578,18 @@ def measure_inverse(dev, iters):
     target medium
     plus 10 % seeded noise, L-BFGS-B on the absorption within [0.1, 1]
     /cm from the background, with the 16 beams as single sources (TS) and
-    as 4 staggered groups (MSS).  Reports E(i), J and the wall time."""
+    as 4 staggered groups (MSS), the latter also driven by the exact
+    discrete gradient instead of the paper's continuous adjoint.  Reports
+    E(i), J and the wall time."""
     import torch
     from paper_2202_09421_gb300 import binding as B
     from paper_2202_09421_gb300.inverse import gpu_evaluator, node_areas, reconstruct
     from paper_2202_09421_gb300.solver import FCDOMSolver
     from rte_inputs import add_relative_noise, workload_inverse
     out = {}
-    for mode in ("ts", "mss"):
-        wl, tgt = workload_inverse(mode), workload_inverse(mode, target=True)
+    for mode, exact in (("ts", False), ("mss", False), ("mss_exact", True)):
+        base = mode.split("_")[0]
+        wl, tgt = workload_inverse(base), workload_inverse(base, target=True)
         mus = torch.tensor(wl.mus, dtype=torch.float32, device=dev)
         st = FCDOMSolver(tgt.grid, tgt.optics, torch.tensor(tgt.mua, dtype=torch.float32, device=dev), mus,
                          tgt.c, tgt.dt, precision=B.RTE_PREC_TF32X3)
@@ -596,12 +599,13 @@ def measure_inverse(dev, iters):
         meas = torch.tensor(add_relative_noise(clean, 0.10), dtype=torch.float32, device=dev)
         solver = FCDOMSolver(wl.grid, wl.optics, torch.tensor(wl.mua, dtype=torch.float32, device=dev), mus,
                              wl.c, wl.dt, ckpt_interval=100, precision=B.RTE_PREC_TF32X3)
-        ev = gpu_evaluator(solver, wl.groups, wl.n_steps, wl.detectors, meas, mus)
+        ev = gpu_evaluator(solver, wl.groups, wl.n_steps, wl.detectors, meas, mus, exact=exact)
         res = reconstruct(ev, wl.mua, 0.1, 1.0, max_iter=iters, a_true=tgt.mua, area=node_areas(wl.grid))
         solver.close()
         hist = res["history"]
         secs = hist[-1]["seconds"]
-        out[mode] = {"groups": len(wl.groups), "iterations": len(hist) - 1, "objective_evaluations": res["nfev"],
+        out[mode] = {"groups": len(wl.groups), "gradient": "exact discrete adjoint" if exact else "continuous adjoint",
+                     "iterations": len(hist) - 1, "objective_evaluations": res["nfev"],
                      "seconds": secs, "seconds_per_evaluation": secs / max(1, res["nfev"]),
                      "E": [h["E"] for h in hist], "J": [h["J"] for h in hist],
                      "seconds_at_iteration": [h["seconds"] for h in hist]}
