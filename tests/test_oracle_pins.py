@@ -441,22 +441,18 @@ def test_subdomain_derivative_converges():
 
 
 # ------------------------------------------------------------ brute force
-def test_brute_force_dense_march_on_tiny_grid():
-    """The whole scheme on a 12 x 10 grid with M = 8 as one dense linear map
-    of the (nx ny M)-vector, assembled from the definitions: eq. (RTEAB4L)
-    as Kronecker products (scattering P~ over ordinates at each node, D_x
-    along i, D_y along j, the local a, b), the boundary condition of eq.
-    (RTE) as a matrix found by geometry (incoming where theta.nu < 0, the
-    governing face at a corner the larger |theta.nu|, the y-face on a tie,
-    the reflected ordinate the one whose direction is the mirror image),
-    and AB4 (eq. RTEAB4) from zero start levels.  The oracle's per-line
-    march must agree to rounding at every step."""
+def _dense_scheme(wl):
+    """The step of the scheme on a small grid as dense matrices of the
+    (nx ny M)-vector u[m, j, i], assembled from the definitions: L of eq.
+    (RTEAB4L) as Kronecker products (scattering P~ over ordinates at each
+    node, D_x along i, D_y along j, the local a, b), and the boundary
+    condition of eq. (RTE) as a matrix found by geometry (incoming where
+    theta.nu < 0, the governing face at a corner the larger |theta.nu|, the
+    y-face on a tie, the reflected ordinate the one whose direction is the
+    mirror image), with the rows it imposes (Gamma_-, where the source
+    enters)."""
     from oracle.fcgram import fc_derivative
-    wl = workload_custom(12, 10, 8, 30, 0.04, L=11 / 66, mus=20.0, n_groups=1, t_s=0.5, sigma_t=0.3)
     g, M = wl.grid, wl.grid.M
-    S = rte.Solver(wl)
-    ref = S.forward(wl.groups[0], wl.n_steps, keep_states=True)["states"]
-
     nn = g.nx * g.ny
     th = 2 * np.pi * np.arange(M) / M
     cx, sy = np.cos(th), np.sin(th)
@@ -468,10 +464,9 @@ def test_brute_force_dense_march_on_tiny_grid():
     Lmat = (b_rep[:, None] * np.kron(P, np.eye(nn)) - np.diag(a_rep + b_rep)
             - np.kron(np.diag(cx), np.kron(np.eye(g.ny), Dx))
             - np.kron(np.diag(sy), np.kron(Dy, np.eye(g.nx))))
-
     normals = {0: (-1.0, 0.0), 1: (1.0, 0.0), 2: (0.0, -1.0), 3: (0.0, 1.0)}
     Bmat = np.eye(M * nn)
-    imposed = np.zeros(M * nn, dtype=bool)          # Gamma_-: the source enters only here
+    imposed = np.zeros(M * nn, dtype=bool)
     for j in range(g.ny):
         for i in range(g.nx):
             faces = [F for F, on in ((0, i == 0), (1, i == g.nx - 1), (2, j == 0), (3, j == g.ny - 1)) if on]
@@ -489,13 +484,41 @@ def test_brute_force_dense_march_on_tiny_grid():
                 imposed[row] = True
                 Bmat[row, :] = 0.0
                 Bmat[row, mr * nn + j * g.nx + i] = rte.fresnel(abs(dots[F]), wl.optics.n_in, wl.optics.n_out)
+    return Lmat, Bmat, imposed
 
+
+def _dense_readout(wl):
+    """eq. (OpMed) as a [detector x state] matrix: per face, trapezoid weight
+    along the face x detector window x sum over outgoing ordinates of
+    w (1 - f) theta.nu."""
+    g, M = wl.grid, wl.grid.M
+    nn = g.nx * g.ny
+    th = 2 * np.pi * np.arange(M) / M
+    X = g.xmin + g.dx * np.arange(g.nx)
+    Y = g.ymin + g.dy * np.arange(g.ny)
+    R = np.zeros((len(wl.detectors), M * nn))
+    faces = (((-1.0, 0.0), [(j, 0) for j in range(g.ny)], g.dy), ((1.0, 0.0), [(j, g.nx - 1) for j in range(g.ny)], g.dy),
+             ((0.0, -1.0), [(0, i) for i in range(g.nx)], g.dx), ((0.0, 1.0), [(g.ny - 1, i) for i in range(g.nx)], g.dx))
+    for nu, nodes, h in faces:
+        cosv = nu[0] * np.cos(th) + nu[1] * np.sin(th)
+        out = cosv > 1e-12
+        wm = np.where(out, (2 * np.pi / M) * (1 - rte.fresnel(np.abs(cosv), wl.optics.n_in, wl.optics.n_out)) * cosv, 0)
+        for k, (j, i) in enumerate(nodes):
+            trap = h * (0.5 if k in (0, len(nodes) - 1) else 1.0)
+            for d, det in enumerate(wl.detectors):
+                wd = trap * rte.window(np.hypot(X[i] - det.x, Y[j] - det.y) / det.sigma_d)
+                R[d, np.arange(M) * nn + j * g.nx + i] += wd * wm
+    return R
+
+
+def _dense_march(wl, S, Lmat, Bmat, imposed):
+    g, M = wl.grid, wl.grid.M
     ab4 = np.array([55.0, -59.0, 37.0, -9.0]) / 24.0
     bj, bi = S.bt.nodes_j, S.bt.nodes_i
-    u = np.zeros(M * nn)
+    u = np.zeros(M * g.nx * g.ny)
     hist = [np.zeros_like(u) for _ in range(3)]
     cdt = wl.c * wl.dt
-    worst = 0.0
+    states = [u]
     for s in range(wl.n_steps):
         Lk = Lmat @ u
         pre = u + cdt * (ab4[0] * Lk + ab4[1] * hist[0] + ab4[2] * hist[1] + ab4[3] * hist[2])
@@ -503,7 +526,58 @@ def test_brute_force_dense_march_on_tiny_grid():
         q[:, bj, bi] = S.beam_inflow(wl.groups[0], (4 + s) * wl.dt).T
         u = Bmat @ pre + np.where(imposed, q.ravel(), 0.0)
         hist = [Lk, hist[0], hist[1]]
-        worst = max(worst, np.abs(u - ref[s].ravel()).max() / np.abs(ref[s]).max())
-    assert np.abs(ref[-1]).max() > 0
-    print(f"dense march vs oracle: {worst:.1e}")
-    assert worst < 1e-11, worst
+        states.append(u)
+    return states
+
+
+def test_brute_force_dense_march_on_tiny_grid():
+    """The whole scheme on a 12 x 10 grid with M = 8 as one dense linear map
+    of the state (`_dense_scheme`), marched with AB4 (eq. RTEAB4) from zero
+    start levels: the oracle's per-line march must agree to rounding at every
+    step, and its detector curves with the dense readout of eq. (OpMed)."""
+    wl = workload_custom(12, 10, 8, 30, 0.04, L=11 / 66, mus=20.0, n_groups=1, t_s=0.5, sigma_t=0.3)
+    S = rte.Solver(wl)
+    out = S.forward(wl.groups[0], wl.n_steps, wl.detectors, keep_states=True)
+    states = _dense_march(wl, S, *_dense_scheme(wl))
+    worst = max(np.abs(states[s + 1] - out["states"][s].ravel()).max() / np.abs(out["states"][s]).max()
+                for s in range(wl.n_steps))
+    R = _dense_readout(wl)
+    curves = np.stack([R @ u for u in states[1:]], axis=1)
+    ec = np.abs(curves - out["curves"]).max() / np.abs(out["curves"]).max()
+    print(f"dense march vs oracle: state {worst:.1e}, curves {ec:.1e}")
+    assert np.abs(out["states"][-1]).max() > 0
+    assert worst < 1e-11 and ec < 1e-9, (worst, ec)
+
+
+def test_brute_force_discrete_gradient_on_tiny_grid():
+    """The exact gradient of the discrete objective by forward-mode
+    sensitivities of the dense march: for every node n, the perturbation of
+    a at n changes L by -u at that node, and dJ/da_n = sum_s dt r^s . R du^s.
+    The oracle's reverse sweep (discrete_adjoint_gradient) must give the same
+    gradient to rounding."""
+    wl = workload_custom(12, 10, 8, 24, 0.04, L=11 / 66, mus=20.0, n_groups=1, t_s=0.5, sigma_t=0.3)
+    tgt = workload_custom(12, 10, 8, 24, 0.04, L=11 / 66, mus=20.0, n_groups=1, t_s=0.5, sigma_t=0.3, seed=5)
+    meas = rte.Solver(tgt).forward(tgt.groups[0], 24, tgt.detectors)["curves"] * 0.8
+    S = rte.Solver(wl)
+    Lmat, Bmat, imposed = _dense_scheme(wl)
+    states = _dense_march(wl, S, Lmat, Bmat, imposed)
+    R = _dense_readout(wl)
+    resid = np.stack([R @ u for u in states[1:]], axis=1) - meas
+    g, M = wl.grid, wl.grid.M
+    nn = g.nx * g.ny
+    sel = np.tile(np.eye(nn), (M, 1))                       # row (m, node) -> column node
+    ab4 = np.array([55.0, -59.0, 37.0, -9.0]) / 24.0
+    cdt = wl.c * wl.dt
+    dU = np.zeros((M * nn, nn))                             # column n: du for a perturbation at node n
+    dH = [np.zeros_like(dU) for _ in range(3)]
+    grad = np.zeros(nn)
+    for s in range(wl.n_steps):
+        dL = Lmat @ dU - states[s][:, None] * sel
+        dU = Bmat @ (dU + cdt * (ab4[0] * dL + ab4[1] * dH[0] + ab4[2] * dH[1] + ab4[3] * dH[2]))
+        dH = [dL, dH[0], dH[1]]
+        grad += wl.dt * (resid[:, s] @ (R @ dU))
+    _, ga, _ = S.discrete_adjoint_gradient(wl.groups[0], wl.n_steps, wl.detectors, meas)
+    err = np.linalg.norm(ga.ravel() - grad) / np.linalg.norm(grad)
+    print(f"reverse sweep vs dense forward-mode gradient: {err:.1e}")
+    assert np.linalg.norm(grad) > 0
+    assert err < 1e-9, err
