@@ -257,6 +257,19 @@ rte_status rte_host_fc_operator(int n, double h, double alpha, double beta, doub
 rte_status rte_host_fc_operator_parts(int n, double h, double alpha, double beta, int parts,
                                       double* D_out);
 rte_status rte_host_phase_matrix(int M, double g, double exponent, double* P_out);
+/* The transpose of the linear part of the boundary map of eq. (RTE) that
+ * rte_discrete_adjoint_gradient applies, for M ordinates and the refractive
+ * indices n_in -> n_out.  Tables 0..3 are the faces (left, right, bottom,
+ * top), 4..7 the corners ((left, bottom), (right, bottom), (left, top),
+ * (right, top)).  On a node of table t, the transposed map takes ubar[M] to
+ * w[k] = sum_{q < 4} f_out[(t M + k) 4 + q] ubar[src_out[(t M + k) 4 + q]]:
+ * slot 0 is the node's own value (f = 1 where ordinate k is not imposed,
+ * 0 where it is), slots 1..3 the imposed ordinates that reflect into k with
+ * their Fresnel coefficient (f = 0 in unused slots).  src_out and f_out hold
+ * 8 * M * 4 entries (host).  Errors: INVALID_ARG (M odd or below 2, null
+ * pointers, indices not positive), UNSUPPORTED (an ordinate that is the
+ * reflection of more than three imposed ordinates). */
+rte_status rte_host_bc_transpose(int M, double n_in, double n_out, int* src_out, double* f_out);
 
 /* Per-kernel timing with CUDA events on the context's stream.  While on,
  * every AB4 step records events around its two passes (x-pass: scattering

@@ -67,7 +67,8 @@ EXPORTS = ("rte_init_medium", "rte_set_medium", "rte_forward", "rte_detector_rea
            "rte_destroy", "rte_status_string", "rte_host_fc_operator", "rte_host_phase_matrix",
            "rte_set_kernel_timing", "rte_kernel_times", "rte_forward_static", "rte_forward_batch",
            "rte_graph_captures", "rte_set_pass_variant", "rte_last_cuda_error",
-           "rte_autotune", "rte_host_fc_operator_parts", "rte_discrete_adjoint_gradient")
+           "rte_autotune", "rte_host_fc_operator_parts", "rte_discrete_adjoint_gradient",
+           "rte_host_bc_transpose")
 
 _lib = None
 
@@ -98,6 +99,7 @@ def library() -> ctypes.CDLL:
         "rte_host_fc_operator": [c_int, c_double, c_double, c_double, P],
         "rte_host_phase_matrix": [c_int, c_double, c_double, P],
         "rte_host_fc_operator_parts": [c_int, c_double, c_double, c_double, c_int, P],
+        "rte_host_bc_transpose": [c_int, c_double, c_double, P, P],
         "rte_set_kernel_timing": [P, c_int],
         "rte_kernel_times": [P, POINTER(c_double), POINTER(c_longlong)],
         "rte_forward_static": [P, POINTER(RteSourceGroup), c_int, c_int, POINTER(RteDetector), c_int, P],
@@ -289,6 +291,16 @@ def rte_host_phase_matrix(M: int, g: float, exponent: float = 1.5):
     _check(library().rte_host_phase_matrix(M, g, exponent, c_void_p(out.ctypes.data)),
            "rte_host_phase_matrix")
     return out
+
+
+def rte_host_bc_transpose(M: int, n_in: float = 1.4, n_out: float = 1.0):
+    """(src [8][M][4] int, f [8][M][4] float64): the transposed boundary map."""
+    import numpy as np
+    src = np.zeros((8, M, 4), dtype=np.int32)
+    f = np.zeros((8, M, 4), dtype=np.float64)
+    _check(library().rte_host_bc_transpose(M, n_in, n_out, c_void_p(src.ctypes.data), c_void_p(f.ctypes.data)),
+           "rte_host_bc_transpose")
+    return src, f
 
 
 def rte_set_kernel_timing(ctx, on: bool):

@@ -643,6 +643,18 @@ rte_status rte_host_phase_matrix(int M, double g, double exponent, double* P_out
   return RTE_OK;
 }
 
+rte_status rte_host_bc_transpose(int M, double n_in, double n_out, int* src_out, double* f_out) {
+  if (M < 2 || M % 2 != 0 || !src_out || !f_out || !(n_in > 0) || !(n_out > 0)) return RTE_ERR_INVALID_ARG;
+  rte_setup::BoundaryTables bt;
+  rte_setup::boundary_tables(M, n_in, n_out, bt);
+  std::vector<int> src;
+  std::vector<double> f;
+  if (!rte_setup::bc_transpose_tables(bt, M, src, f)) return RTE_ERR_UNSUPPORTED;
+  std::memcpy(src_out, src.data(), src.size() * sizeof(int));
+  std::memcpy(f_out, f.data(), f.size() * sizeof(double));
+  return RTE_OK;
+}
+
 rte_status rte_destroy(rte_ctx* c) {
   if (!c) return RTE_ERR_INVALID_ARG;
   cudaStreamSynchronize(c->stream);

@@ -123,3 +123,28 @@ def test_host_decomposed_operator_rejects_short_segments(B):
     with pytest.raises(B.RTEError) as err:
         B.rte_host_fc_operator_parts(40, 0.05, 4)      # owned ranges of 10 -> segments of 12-14 points
     assert err.value.status == 1
+
+
+@pytest.mark.parametrize("M", [8, 16, 32])
+def test_host_bc_transpose_matches_oracle(B, M):
+    """The library's transposed boundary table (what the discrete adjoint
+    gathers through) against the oracle's transposed boundary map, pinned by
+    the dot-product identity: at every boundary node of a grid, on a random
+    field."""
+    from oracle.rte import Solver
+    from rte_inputs import workload_custom
+    wl = workload_custom(16, 18, M, 4, 0.04)
+    src, f = B.rte_host_bc_transpose(M, wl.optics.n_in, wl.optics.n_out)
+    ubar = np.random.default_rng(M).standard_normal((M, wl.grid.ny, wl.grid.nx))
+    ref = Solver(wl).bc_transpose(ubar)
+    nx, ny = wl.grid.nx, wl.grid.ny
+    worst = 0.0
+    for j in range(ny):
+        for i in range(nx):
+            lf, rt, bt, tp = i == 0, i == nx - 1, j == 0, j == ny - 1
+            if not (lf or rt or bt or tp):
+                continue
+            t = 4 + rt + 2 * tp if (lf or rt) and (bt or tp) else (0 if lf else 1 if rt else 2 if bt else 3)
+            w = (f[t] * ubar[src[t], j, i]).sum(axis=1)
+            worst = max(worst, np.abs(w - ref[:, j, i]).max())
+    assert worst < 1e-13, worst
