@@ -16,6 +16,13 @@ Every function restates the paper's method in its own order and notation:
   normalisation; Sec. 4.2 eqs. (RTEAB4)/(RTEAB4L): Adams-Bashforth 4;
   Sec. 4.3 eqs. (RTEFCSum), (FFilter), (RTEFCSumder): FC-Gram continuation
   and the filtered spectral derivative; Algorithm 1: loop order.
+* Sec. 4.4 / Algorithm 1: the subdomain decomposition with two fringe
+  points (fcgram.fc_derivative_parts, Solver(fc_parts=...)).
+* The exact discrete adjoint and the tangent-linear march of the discrete
+  scheme (Solver.discrete_adjoint_gradient, tangent_linear_objective): the
+  transpose of eqs. (RTEAB4)/(RTE)/(OpMed)/(FObj) as discretised, an
+  extension of Sec. 3.4 pinned by the dot-product identity, central
+  differences and a dense brute-force sensitivity on a tiny grid.
 
 Floating point is FP64 throughout; numpy's FFT serves as the FFT step.
 """
