@@ -148,3 +148,19 @@ def test_host_bc_transpose_matches_oracle(B, M):
             w = (f[t] * ubar[src[t], j, i]).sum(axis=1)
             worst = max(worst, np.abs(w - ref[:, j, i]).max())
     assert worst < 1e-13, worst
+
+
+def test_header_is_plain_c():
+    """include/rte.h is a C ABI: it compiles as C99 (and as C++) with no
+    other header of this project and no torch or CUDA types."""
+    import shutil
+    import subprocess
+    hdr = os.path.join(ROOT, "include", "rte.h")
+    for compiler, lang, std in (("gcc", "c", "-std=c99"), ("g++", "c++", "-std=c++17")):
+        if shutil.which(compiler) is None:
+            pytest.skip(f"{compiler} not available")
+        out = subprocess.run([compiler, "-fsyntax-only", "-x", lang, std, "-Wall", "-Wextra", "-Werror", hdr],
+                             capture_output=True, text=True)
+        assert out.returncode == 0, out.stderr
+    includes = [ln for ln in open(hdr) if ln.lstrip().startswith("#include")]
+    assert all("<stddef.h>" in ln or "<stdint.h>" in ln for ln in includes), includes
