@@ -11,7 +11,7 @@ from scipy.special import i0
 from conftest import golden
 from oracle import fcgram
 from oracle import rte
-from rte_inputs import Grid, Optics, Workload, workload_custom, workload_small
+from rte_inputs import Beam, Grid, Optics, Workload, workload_custom, workload_small
 
 
 # ---------------------------------------------------------------- quadrature
@@ -581,3 +581,119 @@ def test_brute_force_discrete_gradient_on_tiny_grid():
     print(f"reverse sweep vs dense forward-mode gradient: {err:.1e}")
     assert np.linalg.norm(grad) > 0
     assert err < 1e-9, err
+
+
+# ---------------------------------------------------------------- beam sources
+def _source_solver(n=129, M=16, L=4.0):
+    """An oracle solver on [0, L]^2 whose only role is to evaluate the beam
+    sources of eq. (RTEsources2) at its boundary nodes."""
+    grid = Grid(n, n, 0.0, L, 0.0, L, M)
+    wl = Workload("src", grid, Optics(), np.full((n, n), 0.1), np.full((n, n), 10.0), 0.02, 0.01, 0,
+                  [[]], [])
+    return rte.Solver(wl)
+
+
+def _face_values(S, q, face, m):
+    """q[node, m] along one face (nodes in the face's order) with the face's
+    trapezoid weights and node coordinates."""
+    jj, ii, wgt = S.bt.face_nodes[face]
+    index = {(j, i): k for k, (j, i) in enumerate(zip(S.bt.nodes_j, S.bt.nodes_i))}
+    rows = np.array([index[(j, i)] for j, i in zip(jj, ii)])
+    return q[rows, m], wgt, S.X[ii], S.Y[jj]
+
+
+def test_beam_spatial_footprint_is_gaussian_of_spread_sigma_x():
+    """eq. (RTEsources2), spatial factor exp(-|x - x_k|^2 / (2 sigma_x^2)):
+    along the face through a mid-face beam (direction on an ordinate, time at
+    the temporal centre, so the other factors are 1) its integral is
+    sigma_x sqrt(2 pi), its mean the beam position and its variance
+    sigma_x^2 (the trapezoid rule is exact to rounding for a Gaussian this
+    well resolved, and the tails beyond the face ends are below 1e-10)."""
+    S = _source_solver()
+    sig = 0.3
+    bm = Beam(2.0, 0.0, np.pi / 2, sigma_x=sig, t_s=30.0, sigma_t=10.0, tau=5.0)
+    q = S.beam_inflow([bm], 35.0)
+    m_k = S.M // 4                                                  # theta_m = pi / 2
+    v, wgt, xs, _ = _face_values(S, q, 2, m_k)
+    mass = np.sum(wgt * v)
+    assert abs(mass / (sig * np.sqrt(2 * np.pi)) - 1) < 1e-9
+    mean = np.sum(wgt * xs * v) / mass
+    var = np.sum(wgt * (xs - mean) ** 2 * v) / mass
+    assert abs(mean - 2.0) < 1e-12
+    assert abs(var / sig ** 2 - 1) < 1e-8
+    # the other faces are at least 2 cm (6.7 sigma_x) away
+    for F in (0, 1, 3):
+        vf, _, _, _ = _face_values(S, q, F, m_k)
+        assert np.max(np.abs(vf)) < 3e-10
+
+
+@pytest.mark.parametrize("theta_k", [np.pi / 2, 0.0, 0.1, 2 * np.pi - 0.05])
+def test_beam_angular_factor_integral_and_direction(theta_k):
+    """eq. (RTEsources2), angular factor w(|theta - theta_k| / sigma_theta)
+    with the departure taken on the circle: at the beam's own node, at its
+    temporal centre, the trapezoid sum over the ordinates (Sec. 4.1) equals
+    sigma_theta int_{-1}^{1} w(v) dv, and the circular mean of the factor
+    points along theta_k.  Beams near theta = 0 have half their support on
+    the far side of 2 pi; a distance that does not wrap loses it."""
+    S = _source_solver(n=33, M=512)
+    st = np.pi / 4
+    bm = Beam(2.0, 0.0, theta_k, sigma_theta=st, t_s=30.0, sigma_t=10.0)
+    q = S.beam_inflow([bm], 30.0)
+    node = int(np.flatnonzero((S.bt.nodes_j == 0) & (S.bt.nodes_i == 16))[0])   # x = 2, y = 0
+    ang = q[node]
+    theta, w, _, _ = rte.ordinates(S.M)
+    ref, _ = integrate.quad(lambda v: rte.window(np.array([v]))[0], -1.0, 1.0, epsabs=1e-14, limit=200)
+    assert abs(w * ang.sum() / (st * ref) - 1) < 1e-9
+    z = np.sum(w * ang * np.exp(1j * theta))
+    assert abs(np.angle(z * np.exp(-1j * theta_k))) < 1e-9
+
+
+def test_beam_temporal_profiles_centre_spread_and_delay():
+    """T(t - tau) of eq. (RTEsources2): the Gaussian reaches 1 at
+    t = tau + t_s and exp(-1/2) at tau + t_s +- sigma_t, with integral
+    sigma_t sqrt(2 pi); the window profile of eq. (sourcelab) is 1 at the
+    centre, w(1/2) = exp(-4 e^{-2}) at +- sigma_t / 2 and 0 from +- sigma_t
+    on.  Evaluated through the source term at the beam's own node and
+    direction, where q = amplitude T."""
+    S = _source_solver(n=33, M=16)
+    node = int(np.flatnonzero((S.bt.nodes_j == 0) & (S.bt.nodes_i == 16))[0])
+    m_k = S.M // 4
+    amp, ts, sg, tau = 2.5, 30.0, 10.0, 7.0
+    gauss = Beam(2.0, 0.0, np.pi / 2, t_s=ts, sigma_t=sg, tau=tau, amplitude=amp)
+    win = Beam(2.0, 0.0, np.pi / 2, t_s=ts, sigma_t=sg, tau=tau, profile=1, amplitude=amp)
+
+    def T(bm, t):
+        return S.beam_inflow([bm], t)[node, m_k] / amp
+
+    c = tau + ts
+    assert abs(T(gauss, c) - 1) < 1e-15
+    for t in (c - sg, c + sg):
+        assert abs(T(gauss, t) - np.exp(-0.5)) < 1e-15
+    assert abs(T(gauss, ts) - 1) > 0.1                                # the delay matters
+    tt = np.linspace(c - 12 * sg, c + 12 * sg, 4801)
+    vals = np.array([T(gauss, t) for t in tt])
+    assert abs(np.trapezoid(vals, tt) / (sg * np.sqrt(2 * np.pi)) - 1) < 1e-12
+    assert T(win, c) == 1.0
+    for t in (c - sg / 2, c + sg / 2):
+        assert abs(T(win, t) - np.exp(-4 * np.exp(-2))) < 1e-15
+    for t in (c - sg, c + sg, c + 1.5 * sg):
+        assert T(win, t) == 0.0
+
+
+def test_two_beams_on_one_face_superpose():
+    """eq. (RTEsources): a generalized source is the sum of its beams.  Two
+    beams on the bottom face with amplitudes A1, A2 and staggered delays
+    give, along that face, the integral sigma_x sqrt(2 pi) (A1 T1 + A2 T2)
+    and the first moment (A1 T1 x1 + A2 T2 x2) / (A1 T1 + A2 T2), with
+    T1 = 1 at the first beam's centre and T2 = exp(-(tau1 - tau2)^2 /
+    (2 sigma_t^2)) there."""
+    S = _source_solver()
+    sig, ts, sg = 0.2, 30.0, 10.0
+    b1 = Beam(1.4, 0.0, np.pi / 2, sigma_x=sig, t_s=ts, sigma_t=sg, tau=0.0, amplitude=1.0)
+    b2 = Beam(2.6, 0.0, np.pi / 2, sigma_x=sig, t_s=ts, sigma_t=sg, tau=6.0, amplitude=0.6)
+    q = S.beam_inflow([b1, b2], ts)
+    v, wgt, xs, _ = _face_values(S, q, 2, S.M // 4)
+    w1, w2 = 1.0, 0.6 * np.exp(-36.0 / (2 * sg ** 2))
+    mass = np.sum(wgt * v)
+    assert abs(mass / (sig * np.sqrt(2 * np.pi) * (w1 + w2)) - 1) < 1e-9
+    assert abs(np.sum(wgt * xs * v) / mass - (w1 * 1.4 + w2 * 2.6) / (w1 + w2)) < 1e-9
