@@ -76,9 +76,13 @@ typedef struct rte_optics {
  *   RTE_PREC_BF16X3 tcgen05 kind::f16 with BF16 operands split hi + lo, three
  *                   products (about 2^-16 relative per product);
  *   RTE_PREC_BF16   tcgen05, single BF16 product.
- * All tensor-core forms accumulate in FP32.  They synchronise the stream at
- * the end of rte_forward and rte_adjoint_gradient to read their timeout flag
- * (RTE_ERR_TIMEOUT). */
+ * All tensor-core forms accumulate in FP32.  Every wait inside their kernels
+ * is bounded; one that runs out sets the context's device timeout word, and
+ * the passes launched while it is set return at once.  They synchronise the
+ * stream at the end of every march (rte_forward, rte_forward_batch, both
+ * adjoint gradients, rte_forward_static) to read and clear that word
+ * (RTE_ERR_TIMEOUT).  Each context has its own word, so a timeout in one
+ * context leaves the others' launches untouched. */
 #define RTE_PREC_FP32 0
 #define RTE_PREC_TF32X3 1
 #define RTE_PREC_TF32 2
@@ -313,6 +317,26 @@ long long rte_graph_captures(const rte_ctx* ctx);
  * in RTE_PREC_FP32).  Errors: INVALID_ARG. */
 rte_status rte_set_pass_variant(rte_ctx* ctx, int variant);
 
+/* Failure injection for tests of the failure path (no counterpart in the
+ * paper; host side, nothing on the device faults or hangs):
+ *   RTE_FAULT_TIMEOUT_WORD  sets the context's timeout word, as a bounded
+ *                           device wait that ran out would: the next march
+ *                           launches tensor-core passes that return at once
+ *                           and reports RTE_ERR_TIMEOUT (clearing the word);
+ *   RTE_FAULT_EXPIRE_WAIT   the next march's first one-tile-per-CTA
+ *                           tensor-core pass (rte_set_pass_variant 1) has one
+ *                           CTA wait on a barrier that nothing arrives on,
+ *                           before it issues any copy or MMA; the bounded
+ *                           wait runs out after about 2 s and the march
+ *                           reports RTE_ERR_TIMEOUT;
+ *   RTE_FAULT_CLEAR         withdraws both.
+ * Errors: INVALID_ARG (unknown kind), UNSUPPORTED (RTE_PREC_FP32: its
+ * kernels have no device waits), CUDA. */
+#define RTE_FAULT_CLEAR 0
+#define RTE_FAULT_TIMEOUT_WORD 1
+#define RTE_FAULT_EXPIRE_WAIT 2
+rte_status rte_inject_fault(rte_ctx* ctx, int kind);
+
 /* Autotuner (no counterpart in the paper): times every kernel configuration
  * the context's precision admits, with CUDA events around one forward of
  * n_trial_steps (>= 4) of the given groups after an untimed one, and keeps
@@ -334,9 +358,13 @@ rte_status rte_autotune(rte_ctx* ctx, const rte_source_group* groups, int n_grou
  * cudaMalloc/cudaFree while they run (device memory already reserved by
  * another allocator, latency-critical loops where an allocation may
  * synchronise the device, or a no-allocation policy after start-up).
- * It computes what rte_forward followed by rte_detector_readout computes
- * (same kernels, same order): curves_out (device FP32 [group][det][step])
- * for n_groups groups of beams over n_steps steps.  All per-call scratch
+ * It computes what rte_forward followed by rte_detector_readout computes,
+ * the same discrete operator marched by the two-pass kernels of the
+ * context's precision and schedule (the tile-local fused step of
+ * rte_set_pass_variant 3 is not used here; it agrees with it to FP32
+ * rounding): curves_out (device FP32 [group][det][step], at least
+ * n_groups * n_det * n_steps floats) for n_groups groups of beams over
+ * n_steps steps.  All per-call scratch
  * (state, history, exitance ring, source and detector tables) lives in one
  * file-scope device array of 64 MiB, reserved on every GPU that loads the
  * library until the process exits; a solve that needs more returns
@@ -347,8 +375,12 @@ rte_status rte_autotune(rte_ctx* ctx, const rte_source_group* groups, int n_grou
  * come before any stream capture.  Every call shares the array and finds the
  * previous call's data there (it zeroes what must start at zero); calls that
  * overlap on the GPU race on it.  Host tables are copied from pageable
- * memory, so the call returns after they have left the host.
- * Errors: INVALID_ARG, UNSUPPORTED (scratch too small), CUDA. */
+ * memory, so the call returns after they have left the host.  The calling
+ * thread's current device must be the context's device (the array's address
+ * is looked up there).  In the tensor-core precisions the call synchronises
+ * the stream at the end to read the context's timeout word.
+ * Errors: INVALID_ARG (also: current device is not the context's),
+ * UNSUPPORTED (scratch too small), CUDA, TIMEOUT. */
 rte_status rte_forward_static(rte_ctx* ctx, const rte_source_group* groups, int n_groups,
                               int n_steps, const rte_detector* dets, int n_det,
                               float* curves_out);

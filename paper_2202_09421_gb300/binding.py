@@ -68,7 +68,7 @@ EXPORTS = ("rte_init_medium", "rte_set_medium", "rte_forward", "rte_detector_rea
            "rte_set_kernel_timing", "rte_kernel_times", "rte_forward_static", "rte_forward_batch",
            "rte_graph_captures", "rte_set_pass_variant", "rte_last_cuda_error",
            "rte_autotune", "rte_host_fc_operator_parts", "rte_discrete_adjoint_gradient",
-           "rte_host_bc_transpose")
+           "rte_host_bc_transpose", "rte_inject_fault")
 
 _lib = None
 
@@ -106,6 +106,7 @@ def library() -> ctypes.CDLL:
         "rte_forward_batch": [POINTER(c_void_p), c_int, POINTER(POINTER(RteSourceGroup)), POINTER(c_int), c_int],
         "rte_graph_captures": [P],
         "rte_set_pass_variant": [P, c_int],
+        "rte_inject_fault": [P, c_int],
         "rte_last_cuda_error": [],
         "rte_autotune": [P, POINTER(RteSourceGroup), c_int, c_int, POINTER(c_int), POINTER(ctypes.c_float)],
     }
@@ -319,6 +320,9 @@ def rte_forward_static(ctx, groups, n_steps: int, dets, curves_out):
     """Forward solve and detector curves without any device allocation: all
     per-call scratch sits in the library's 64 MiB static device array (for
     callers that cannot call cudaMalloc while they run; see include/rte.h)."""
+    need = len(groups) * len(dets) * int(n_steps)
+    if curves_out.numel() < need:
+        raise ValueError(f"curves_out holds {curves_out.numel()} floats; [group][det][step] needs {need}")
     beam_arrays = [make_beams(bl) for bl in groups]
     garr = (RteSourceGroup * len(groups))()
     for k, bl in enumerate(groups):
@@ -326,6 +330,16 @@ def rte_forward_static(ctx, groups, n_steps: int, dets, curves_out):
     _check(library().rte_forward_static(ctx, garr, len(groups), int(n_steps), make_detectors(dets),
                                         len(dets), _dev_ptr(curves_out, "curves_out")),
            "rte_forward_static")
+
+
+RTE_FAULT_CLEAR, RTE_FAULT_TIMEOUT_WORD, RTE_FAULT_EXPIRE_WAIT = 0, 1, 2
+
+
+def rte_inject_fault(ctx, kind: int):
+    """Host-side failure injection for tests of the timeout path (see
+    include/rte.h): set the context's timeout word, or make the next march's
+    first tensor-core pass run one bounded wait out."""
+    _check(library().rte_inject_fault(ctx, int(kind)), "rte_inject_fault")
 
 
 def rte_destroy(ctx):

@@ -44,6 +44,11 @@ struct rte_ctx {
   int fused_own_max = 0;
   bool fused_exact = true;          // every part owns kFusedOwnMax points
   int tc_mode = 0;                 // the precision: 0 SIMT FP32, 1-4 tcgen05 forms
+  int device = 0;                  // the CUDA device current at creation
+  // timeout word of the tensor-core passes (one device int, see tc_check)
+  // and the test-only request that the next march's first pass time out
+  DevBuf err;
+  bool inject_expire = false;
   int x_variant = 1;               // pass kernels: 0 persistent warp-specialised, 1 one tile per CTA, 2 pipelined y-pass
   // state of the last forward
   int G = 0, n_steps = -1, kmax = 0;
@@ -175,6 +180,8 @@ rte_kern::StepArgs step_args(rte_ctx* c, int G) {
   a.FyT = F(c->FyT);
   a.fused_own_max = c->fused_own_max;
   a.fused_exact = c->fused_exact ? 1 : 0;
+  a.err = static_cast<int*>(c->err.p);
+  a.test_expire = c->inject_expire ? 1 : 0;
   return a;
 }
 
@@ -344,16 +351,20 @@ rte_status ensure_transposed(rte_ctx* c) {
   return RTE_OK;
 }
 
-// The tcgen05 kernels bound every wait and raise a device flag instead of
-// hanging; the tensor-core forms synchronise at the end of a march to read it.
+// The tcgen05 kernels bound every wait and, when one runs out, set the
+// context's timeout word instead of hanging; passes launched while it is set
+// return at once.  The tensor-core forms synchronise at the end of a march to
+// read it, and clear it.
 rte_status tc_check(rte_ctx* c) {
+  c->inject_expire = false;
   if (c->tc_mode == 0) return RTE_OK;
+  int flag = 0;
+  RTE_TRY(cuda_status(cudaMemcpyAsync(&flag, c->err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream)));
   RTE_TRY(cuda_status(cudaStreamSynchronize(c->stream)));
-  int flag = 0, flag_ws = 0, flag_pipe = 0;
-  RTE_TRY(cuda_status(rte_kern::tc_take_error(&flag)));
-  RTE_TRY(cuda_status(rte_kern::ws_take_error(&flag_ws)));
-  RTE_TRY(cuda_status(rte_kern::pipe_take_error(&flag_pipe)));
-  return (flag || flag_ws || flag_pipe) ? RTE_ERR_TIMEOUT : RTE_OK;
+  if (!flag) return RTE_OK;
+  RTE_TRY(cuda_status(cudaMemsetAsync(c->err.p, 0, sizeof(int), c->stream)));
+  RTE_TRY(cuda_status(cudaStreamSynchronize(c->stream)));
+  return RTE_ERR_TIMEOUT;
 }
 
 // Split, swizzled phase matrix for the tensor-core scattering contraction
@@ -500,6 +511,7 @@ void append_forward_key(const rte_ctx* c, std::vector<unsigned long long>& key) 
   key.push_back(static_cast<unsigned long long>(c->kmax));
   key.push_back(static_cast<unsigned long long>(c->x_variant));
   key.push_back(static_cast<unsigned long long>(c->par.flags));
+  key.push_back(static_cast<unsigned long long>(c->inject_expire));
   for (const void* p : ptrs) key.push_back(key_ptr(p));
 }
 
@@ -533,6 +545,13 @@ rte_status rte_set_pass_variant(rte_ctx* c, int variant) {
   if (!c || variant < 0 || variant > 3) return RTE_ERR_INVALID_ARG;
   c->x_variant = variant;
   return RTE_OK;
+}
+
+rte_status rte_inject_fault(rte_ctx* c, int kind) {
+  if (!c || kind < RTE_FAULT_CLEAR || kind > RTE_FAULT_EXPIRE_WAIT) return RTE_ERR_INVALID_ARG;
+  if (c->tc_mode == 0) return RTE_ERR_UNSUPPORTED;   // the FP32 kernels have no device waits
+  c->inject_expire = kind == RTE_FAULT_EXPIRE_WAIT;
+  return cuda_status(cudaMemsetAsync(c->err.p, kind == RTE_FAULT_TIMEOUT_WORD ? 1 : 0, sizeof(int), c->stream));
 }
 
 rte_status rte_autotune(rte_ctx* c, const rte_source_group* groups, int n_groups, int n_trial_steps,
@@ -668,6 +687,7 @@ rte_status rte_destroy(rte_ctx* c) {
                    &c->bct_src, &c->bct_f, &c->fxp, &c->fyp, &c->FxT, &c->FyT};
   for (DevBuf* b : all) release(*b);
   release(c->batch_tab);
+  release(c->err);
   for (cudaEvent_t e : c->events) cudaEventDestroy(e);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   for (cudaEvent_t e : c->gev)
@@ -720,6 +740,11 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
   c->par = *p;
   c->stream = static_cast<cudaStream_t>(stream);
   c->tc_mode = p->precision;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return RTE_ERR_CUDA;
+  }
   c->plane = static_cast<size_t>(g->nx) * g->ny * g->M;
   c->ring_len = 2 * g->nx + 2 * g->ny;
   auto fail = [&](rte_status s) { rte_destroy(c); return s; };
@@ -792,8 +817,9 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
       double wy = (j == 0 || j == g->ny - 1) ? 0.5 * c->dy : c->dy;
       area[static_cast<size_t>(j) * g->nx + i] = static_cast<float>(wx * wy);
     }
-  rte_status s = RTE_OK;
-  if (c->tc_mode != 0 && (p->flags & RTE_FLAG_TC_SCATTER)) s = ensure_phase_image(c);
+  rte_status s = ensure(c->err, sizeof(int));
+  if (s == RTE_OK) s = cuda_status(cudaMemsetAsync(c->err.p, 0, sizeof(int), c->stream));
+  if (s == RTE_OK && c->tc_mode != 0 && (p->flags & RTE_FLAG_TC_SCATTER)) s = ensure_phase_image(c);
   if (s == RTE_OK) s = upload(c->PT, PTf, c->stream);
   if (s == RTE_OK) s = upload(c->xi, xi, c->stream);
   if (s == RTE_OK) s = upload(c->eta, eta, c->stream);
@@ -918,7 +944,12 @@ rte_status rte_forward_batch(rte_ctx* const* ctxs, int n_ctx, const rte_source_g
     }));
   }
   for (int i = 0; i < n_ctx; ++i) ctxs[i]->hl = (2 * n_steps) % 3;
-  return tc_check(c0);
+  rte_status st = RTE_OK;
+  for (int i = 0; i < n_ctx; ++i) {
+    const rte_status si = tc_check(ctxs[i]);
+    if (st == RTE_OK) st = si;
+  }
+  return st;
 }
 
 rte_status rte_detector_readout(rte_ctx* c, const rte_detector* dets, int n_det, float* curves_out) {
@@ -1226,6 +1257,14 @@ extern "C" rte_status rte_forward_static(rte_ctx* c, const rte_source_group* gro
                                          float* curves_out) {
   if (!c || !groups || n_groups <= 0 || n_steps <= 0 || !dets || n_det <= 0 || !curves_out)
     return RTE_ERR_INVALID_ARG;
+  // The array's address is looked up on the current device; the kernels run
+  // on the context's stream, which belongs to the context's device.
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return RTE_ERR_CUDA;
+  }
+  if (dev != c->device) return RTE_ERR_INVALID_ARG;
   int kmax = 0;
   for (int g = 0; g < n_groups; ++g) {
     if (groups[g].n_beams < 0 || (groups[g].n_beams > 0 && !groups[g].beams)) return RTE_ERR_INVALID_ARG;
@@ -1306,6 +1345,8 @@ extern "C" rte_status rte_forward_static(rte_ctx* c, const rte_source_group* gro
                                               c->stream, &c->launches)));
     hl = (hl + 2) % 3;
   }
-  return cuda_status(rte_kern::launch_readout(ring, c->ring_len, n_steps, G, Wdd, lohi_d, lohi_d + n_det,
-                                              n_det, curves_out, nullptr, c->stream, &c->launches));
+  RTE_TRY(cuda_status(rte_kern::launch_readout(ring, c->ring_len, n_steps, G, Wdd, lohi_d, lohi_d + n_det,
+                                               n_det, curves_out, nullptr, c->stream, &c->launches)));
+  // tensor-core forms: read (and clear) the context's timeout word
+  return tc_check(c);
 }

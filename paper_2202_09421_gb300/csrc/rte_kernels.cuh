@@ -73,6 +73,16 @@ struct StepArgs {
   const float* FyT;
   int fused_own_max;                // largest owned range over both axes
   int fused_exact;                  // every part owns exactly kFusedOwnMax points
+  // The context's timeout word (device int): a tensor-core pass whose
+  // bounded wait runs out sets it to 1, and every tensor-core pass launched
+  // while it is set returns at once; the host reads and clears it after a
+  // march.
+  int* err;
+  // Failure injection for tests: block (0, 0, 0) of the first
+  // one-tile-per-CTA pass of the march waits on a barrier that nothing
+  // arrives on, before it issues any copy or MMA, so that the bounded wait
+  // runs out; the CTA then skips its work.
+  int test_expire;
 };
 
 // Largest owned range per axis of the tile-local fused step.
@@ -111,9 +121,6 @@ void tc_batch_layout(BatchProblem* probs, int n, int* ctas_x, int* ctas_y);
 // probs_dev is a device copy of the host table `probs`.
 cudaError_t launch_step_tc_batched(const BatchProblem* probs, const BatchProblem* probs_dev, int n,
                                    int step, int hl, cudaStream_t s, long long* launches);
-// Reads and clears the tcgen05 kernels' bounded-wait timeout flag
-// (synchronous).
-cudaError_t tc_take_error(int* flag);
 
 // Persistent warp-specialised passes (rte_tc_ws.cu): nx, ny <= 256, M in
 // {16, 32}, without the tensor-core scattering flag.
@@ -121,7 +128,6 @@ bool tc_ws_supported(const StepArgs& a);
 cudaError_t launch_pass_ws(bool xpass, const StepArgs& a, const BoundaryArgs& b, float* U, float* R,
                            const float* L1, const float* L2, float* L3, int src_step, int ring_step,
                            cudaStream_t s);
-cudaError_t ws_take_error(int* flag);
 
 // Pipelined persistent y-pass (rte_tc_pipe.cu): ny <= 256, M in {16, 32, 64};
 // the main loop of one tile and the epilogue of the previous one run on two
@@ -129,7 +135,6 @@ cudaError_t ws_take_error(int* flag);
 bool tc_pipe_supported(const StepArgs& a);
 cudaError_t launch_ypass_pipe(const StepArgs& a, const BoundaryArgs& b, float* U, const float* R, const float* L1,
                               const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s);
-cudaError_t pipe_take_error(int* flag);
 
 // Tile-local fused step (rte_fused.cu): one launch per step over the
 // subdomains of the decomposed operator (parts >= 2 on both axes, owned

@@ -40,27 +40,25 @@
 // threads.  K runs in chunks of one 128-byte row (32 tf32 / 64 bf16
 // positions); the next chunk's slab values are loaded into registers while
 // the tensor core works on the current one.  One thread issues the MMAs
-// and commits them to mbarriers; every wait is bounded and sets g_tc_error
-// instead of spinning forever.
+// and commits them to mbarriers; every wait is bounded and sets the context's
+// timeout word (StepArgs::err) instead of spinning forever.
 #include <cstdint>
 
 #include "rte_tc_common.cuh"
 
 namespace rte_kern {
 
-__device__ int g_tc_error;
-
 namespace {
 
 using namespace tc;
 
-// Bounded wait (kWaitNs of wall clock); false, and the error flag set, when
-// the limit runs out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait (kWaitNs of wall clock); false, and the timeout word set,
+// when the limit runs out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
   const unsigned long long t0 = global_ns();
   while (!mbar_try(bar, parity))
     if (global_ns() - t0 > kWaitNs) {
-      atomicExch(&g_tc_error, 1);
+      atomicExch(err, 1);
       return false;
     }
   return true;
@@ -99,7 +97,7 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
   const int n_lines = XPASS ? ny : nx;        // rows (x) / columns (y) of the grid
 
   // A launch after a timed-out one does nothing (the march reports the error).
-  if (*static_cast<volatile int*>(&g_tc_error)) return;
+  if (*static_cast<volatile int*>(a.err)) return;
   unsigned char* sm = smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023);
   unsigned char* Psm = sm + L.stage_bytes;    // P~ image (x-pass, TC scattering)
   const uint32_t bar_full = smem_u32(&bars[0]), bar_done = smem_u32(&bars[1]);
@@ -120,6 +118,20 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
+  // Failure injection (tests): one CTA waits on a barrier that nothing
+  // arrives on, before this CTA has issued any copy or MMA, so that the
+  // bounded wait runs out and sets the timeout word; the CTA then frees its
+  // tensor memory and leaves without touching any output.
+  if (a.test_expire && tile == 0 && g == 0) {
+    __shared__ int gave_up;
+    if (tid == 0) gave_up = mbar_wait(bar_scat, 0, a.err) ? 0 : 1;
+    __syncthreads();
+    if (gave_up) {
+      if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L.tmem_cols));
+      return;
+    }
+  }
   if constexpr (XPASS && SCAT_TC) {
     if (tid == 0) bulk_copy(smem_u32(Psm), a.PImg, kPBytes, bar_p);
   }
@@ -167,7 +179,7 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
   unsigned char* Slo = Shi + kTileBytes;
   load_chunk(0);
   for (int q = 0; q < L.n_kc; ++q) {
-    if (q >= 1) ok = mbar_wait(bar_done, (q - 1) & 1) && ok;    // stage free again
+    if (q >= 1) ok = mbar_wait(bar_done, (q - 1) & 1, a.err) && ok;    // stage free again
     if (tid == 0) {
       // image chunk: [hi: nrows_img rows][lo: nrows_img rows] -> Dhi, Dlo contiguous
       bulk_copy(smem_u32(Dhi), Dimg + q * chunk_bytes, (X3 ? 2 : 1) * nrows_img * 128, bar_full);
@@ -194,7 +206,7 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
     __syncthreads();
     if (q + 1 < L.n_kc) load_chunk(q + 1);
     if (tid == 0) {
-      ok = mbar_wait(bar_full, q & 1) && ok;
+      ok = mbar_wait(bar_full, q & 1, a.err) && ok;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint64_t dSh = sw128_desc(smem_u32(Shi)), dSl = sw128_desc(smem_u32(Slo));
       if (XPASS) {
@@ -234,7 +246,7 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
       mma_commit(bar_done);
     }
   }
-  ok = mbar_wait(bar_done, (L.n_kc - 1) & 1) && ok;
+  ok = mbar_wait(bar_done, (L.n_kc - 1) & 1, a.err) && ok;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   // ---------------- x-pass: scattering contraction into the same tiles ----------------
@@ -248,7 +260,7 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
     const int slot_bytes = (X3 ? 2 : 1) * kTileBytes;
     const int slots = min(4, L.stage_bytes / slot_bytes);
     const int pairs = L.n_mt * per_tile;
-    if (tid == 0) ok = mbar_wait(bar_p, 0) && ok;
+    if (tid == 0) ok = mbar_wait(bar_p, 0, a.err) && ok;
     const uint64_t dPh = sw128_desc(smem_u32(Psm)), dPl = sw128_desc(smem_u32(Psm + 32 * 128));
     int round = 0;
     for (int p0 = 0; p0 < pairs; p0 += slots, ++round) {
@@ -309,7 +321,7 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
         }
         mma_commit(bar_scat);
       }
-      ok = mbar_wait(bar_scat, round & 1) && ok;
+      ok = mbar_wait(bar_scat, round & 1, a.err) && ok;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
   }
@@ -857,13 +869,6 @@ cudaError_t launch_step_tc(const StepArgs& a, const BoundaryArgs& b, float* U, f
   if (ev) cudaEventRecord(ev[2], s);
   if (launches) *launches += 2;
   return e;
-}
-
-cudaError_t tc_take_error(int* flag) {
-  int zero = 0;
-  cudaError_t e = cudaMemcpyFromSymbol(flag, g_tc_error, sizeof(int));
-  if (e != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int));
 }
 
 }  // namespace rte_kern

@@ -21,14 +21,13 @@
 // The groups synchronise internally with named barriers (1 and 2) and with
 // each other through mbarriers (accumulator full / accumulator free).
 // Every wait is bounded by kWaitNs of %globaltimer; on expiry the kernel
-// raises g_pipe_error and an abort flag that ends the other waits.
+// raises the context's timeout word and an abort flag that ends the other waits.
 #include <cstdint>
 
 #include "rte_tc_common.cuh"
 
 namespace rte_kern {
 
-__device__ int g_pipe_error;
 
 namespace {
 
@@ -45,12 +44,12 @@ constexpr size_t kEpiSmem = static_cast<size_t>(kNBuf) * kChunkFloats * 4 + 3 * 
                             (8 + 4 + 8) * kMaxM * 4 + 8 * kMaxM;
 constexpr int kSmemLimit = 232448 - 2048;
 
-__device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err) {
   const unsigned long long t0 = global_ns();
   while (!mbar_try(bar, parity)) {
     if (*abort_flag) return false;
     if (global_ns() - t0 > kWaitNs) {
-      atomicExch(&g_pipe_error, 1);
+      atomicExch(err, 1);
       *abort_flag = 1;
       return false;
     }
@@ -58,11 +57,11 @@ __device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatil
   return true;
 }
 
-__device__ __forceinline__ bool pipe_wait_plain(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool pipe_wait_plain(uint32_t bar, uint32_t parity, int* err) {
   const unsigned long long t0 = global_ns();
   while (!mbar_try(bar, parity))
     if (global_ns() - t0 > kWaitNs) {
-      atomicExch(&g_pipe_error, 1);
+      atomicExch(err, 1);
       return false;
     }
   return true;
@@ -108,7 +107,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   const int tiles_per_group = (nx + per_tile - 1) / per_tile;
   const int total = tiles_per_group * a.G;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (*static_cast<volatile int*>(&g_pipe_error)) return;
+  if (*static_cast<volatile int*>(a.err)) return;
   const int acc_cols = L.nrows_img;
   unsigned char* sm = smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023);
   float* epi = reinterpret_cast<float*>(sm + L.stage_bytes);
@@ -194,7 +193,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         // The leader waits for the previous chunk's MMAs (the stage is free
         // again) and starts the operator copy; the group follows its result.
         if (gtid == 0) {
-          const bool ok0 = it < 1 || pipe_wait(bar_done, (it - 1) & 1, abrt);
+          const bool ok0 = it < 1 || pipe_wait(bar_done, (it - 1) & 1, abrt, a.err);
           if (ok0) {
             bulk_copy(smem_u32(Dhi), Dimg + q * chunk_bytes, (X3 ? 2 : 1) * L.nrows_img * 128, bar_full);
             ++issued;
@@ -230,8 +229,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         else if (tl + static_cast<int>(gridDim.x) < total) load_chunk(tl + gridDim.x, 0);
         if (gtid == 0) {
           bool ok = true;
-          if (q == 0) ok = pipe_wait(acc_empty(b2), ((titer >> 1) & 1) ^ 1, abrt);   // accumulator free
-          ok = ok && pipe_wait(bar_full, it & 1, abrt);
+          if (q == 0) ok = pipe_wait(acc_empty(b2), ((titer >> 1) & 1) ^ 1, abrt, a.err);   // accumulator free
+          ok = ok && pipe_wait(bar_full, it & 1, abrt, a.err);
           if (ok) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint64_t dSh = sw128_desc(smem_u32(Shi)), dSl = sw128_desc(smem_u32(Slo));
@@ -254,9 +253,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     }
     if (gtid == 0) {
       // every copy has landed and every MMA completed before the CTA leaves
-      if (issued > 0) pipe_wait_plain(bar_full, (issued - 1) & 1);
+      if (issued > 0) pipe_wait_plain(bar_full, (issued - 1) & 1, a.err);
       mma_commit(mma_done);
-      pipe_wait_plain(mma_done, 0);
+      pipe_wait_plain(mma_done, 0, a.err);
     }
   } else {
     // ---------------- epilogue group ----------------
@@ -292,7 +291,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       };
       // the data of the first chunks does not depend on the accumulator
       for (int cc = 0; cc < kNBuf - 1 && cc < nchunks; ++cc) issue_chunk(cc);
-      if (etid == 0) epi_ok = pipe_wait(acc_full(b2), (titer >> 1) & 1, abrt);
+      if (etid == 0) epi_ok = pipe_wait(acc_full(b2), (titer >> 1) & 1, abrt, a.err);
       group_sync(2);
       const bool got = epi_ok;                                     // uniform over the group
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -478,11 +477,5 @@ cudaError_t launch_ypass_pipe(const StepArgs& a, const BoundaryArgs& b, float* U
   }
 }
 
-cudaError_t pipe_take_error(int* flag) {
-  int zero = 0;
-  cudaError_t e = cudaMemcpyFromSymbol(flag, g_pipe_error, sizeof(int));
-  if (e != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(g_pipe_error, &zero, sizeof(int));
-}
 
 }  // namespace rte_kern

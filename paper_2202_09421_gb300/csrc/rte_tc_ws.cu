@@ -26,7 +26,7 @@
 // ordinates sit in adjacent lanes of one warp, so the reflected ordinate of
 // the boundary condition is a warp shuffle and the exitance a shuffled sum
 // in ordinate order.
-// Every wait is bounded: on expiry the kernel raises g_ws_error and a shared
+// Every wait is bounded: on expiry the kernel raises the context timeout word and a shared
 // abort flag that ends every other role's waits, and all roles leave.
 #include <cstdint>
 
@@ -34,7 +34,6 @@
 
 namespace rte_kern {
 
-__device__ int g_ws_error;
 
 namespace {
 
@@ -47,23 +46,23 @@ constexpr int kMaxStages = 4;
 constexpr int kSmemLimit = 232448 - 2048;
 
 // Bounded wait (kWaitNs, no abort check): the drains before the kernel leaves.
-__device__ __forceinline__ bool ws_wait_plain(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool ws_wait_plain(uint32_t bar, uint32_t parity, int* err) {
   const unsigned long long t0 = global_ns();
   while (!mbar_try(bar, parity))
     if (global_ns() - t0 > kWaitNs) {
-      atomicExch(&g_ws_error, 1);
+      atomicExch(err, 1);
       return false;
     }
   return true;
 }
 
 // Bounded wait that also gives up once another role has aborted.
-__device__ __forceinline__ bool ws_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool ws_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err) {
   const unsigned long long t0 = global_ns();
   while (!mbar_try(bar, parity)) {
     if (*abort_flag) return false;
     if (global_ns() - t0 > kWaitNs) {
-      atomicExch(&g_ws_error, 1);
+      atomicExch(err, 1);
       *abort_flag = 1;
       return false;
     }
@@ -109,7 +108,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   const int total = tiles_per_group * a.G;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // A launch after a timed-out one does nothing (the march reports the error).
-  if (*static_cast<volatile int*>(&g_ws_error)) return;
+  if (*static_cast<volatile int*>(a.err)) return;
   const int acc_cols = L.nrows_img;                    // one accumulator buffer (n_mt * 128)
   unsigned char* sm = smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023);
   auto bar = [&](int k) { return smem_u32(&bars[k]); };
@@ -172,14 +171,14 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       for (int tl = blockIdx.x; tl < total; tl += gridDim.x)
         for (int q = 0; q < L.n_kc; ++q, ++it) {
           const int s = it % S;
-          if (!ws_wait(empty(s), ((it / S) & 1) ^ 1, abrt)) goto d_done;
+          if (!ws_wait(empty(s), ((it / S) & 1) ^ 1, abrt, a.err)) goto d_done;
           bulk_copy(smem_u32(stage_ptr(s)), Dimg + q * chunk_bytes, (X3 ? 2 : 1) * nrows_img * 128, full_d(s));
         }
     d_done:
       // the last copy into each stage has landed before the CTA leaves
       for (int k = 0; k < S && k < it; ++k) {
         const int j = it - 1 - k;
-        ws_wait_plain(full_d(j % S), (j / S) & 1);
+        ws_wait_plain(full_d(j % S), (j / S) & 1, a.err);
       }
     }
   } else if (warp == kWarpMMA) {
@@ -194,13 +193,13 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       int it = 0, titer = 0;
       for (int tl = blockIdx.x; tl < total; tl += gridDim.x, ++titer) {
         const int b2 = titer & 1;
-        if (!ws_wait(acc_empty(b2), ((titer >> 1) & 1) ^ 1, abrt)) break;
+        if (!ws_wait(acc_empty(b2), ((titer >> 1) & 1) ^ 1, abrt, a.err)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         bool fine = true;
         for (int q = 0; q < L.n_kc; ++q, ++it) {
           const int s = it % S;
           const uint32_t ph = (it / S) & 1;
-          if (!ws_wait(full_d(s), ph, abrt) || !ws_wait(full_s(s), ph, abrt)) {
+          if (!ws_wait(full_d(s), ph, abrt, a.err) || !ws_wait(full_s(s), ph, abrt, a.err)) {
             fine = false;
             break;
           }
@@ -246,7 +245,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       }
       // every MMA issued by this thread has completed before TMEM is freed
       mma_commit(mma_done);
-      ws_wait_plain(mma_done, 0);
+      ws_wait_plain(mma_done, 0, a.err);
     }
   } else if (warp >= kEpiWarps) {
     // ---------------- slab staging ----------------
@@ -290,7 +289,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       bool fine = true;
       for (int q = 0; q < L.n_kc; ++q, ++it) {
         const int s = it % S;
-        if (!ws_wait(empty(s), ((it / S) & 1) ^ 1, abrt)) {
+        if (!ws_wait(empty(s), ((it / S) & 1) ^ 1, abrt, a.err)) {
           fine = false;
           break;
         }
@@ -339,7 +338,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     int titer = 0;
     for (int tl = blockIdx.x; tl < total; tl += gridDim.x, ++titer) {
       const int b2 = titer & 1;
-      if (!ws_wait(acc_full(b2), (titer >> 1) & 1, abrt)) break;
+      if (!ws_wait(acc_full(b2), (titer >> 1) & 1, abrt, a.err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int g = tl / tiles_per_group, t0 = (tl - g * tiles_per_group) * per_tile;
       const size_t goff = static_cast<size_t>(g) * a.plane;
@@ -397,7 +396,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     int titer = 0;
     for (int tl = blockIdx.x; tl < total; tl += gridDim.x, ++titer) {
       const int b2 = titer & 1;
-      if (!ws_wait(acc_full(b2), (titer >> 1) & 1, abrt)) break;
+      if (!ws_wait(acc_full(b2), (titer >> 1) & 1, abrt, a.err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int g = tl / tiles_per_group, t0 = (tl - g * tiles_per_group) * per_tile;
       const size_t goff = static_cast<size_t>(g) * a.plane;
@@ -565,11 +564,5 @@ cudaError_t launch_pass_ws(bool xpass, const StepArgs& a, const BoundaryArgs& b,
                : launch_ws_pass<false>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
 }
 
-cudaError_t ws_take_error(int* flag) {
-  int zero = 0;
-  cudaError_t e = cudaMemcpyFromSymbol(flag, g_ws_error, sizeof(int));
-  if (e != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(g_ws_error, &zero, sizeof(int));
-}
 
 }  // namespace rte_kern

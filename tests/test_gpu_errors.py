@@ -72,3 +72,78 @@ def test_calls_out_of_order_and_invalid_beams():
     s.close()
     ref = Solver(wl).forward(wl.groups[0], wl.n_steps, wl.detectors)["curves"]
     assert rel_l2(curves[0], ref) < 1e-5
+
+
+# ---------------------------------------------------------------- timeout path
+TIMEOUT, UNSUPPORTED = 5, 7
+TF32X3 = 1
+
+
+def _tc_solver(wl, **kw):
+    from paper_2202_09421_gb300.solver import FCDOMSolver
+    return FCDOMSolver(wl.grid, wl.optics, _t(wl.mua), _t(wl.mus), wl.c, wl.dt, precision=TF32X3, **kw)
+
+
+def _oracle_curves(wl):
+    return Solver(wl).forward(wl.groups[0], wl.n_steps, wl.detectors)["curves"]
+
+
+def test_timeout_word_stops_the_march_and_is_cleared():
+    """A set timeout word (as left by a bounded wait that ran out) makes every
+    tensor-core pass of the march return at once: the call reports TIMEOUT
+    and the state stays at its zero start.  The word is cleared with the
+    report, and the next march on the same context matches the oracle."""
+    from paper_2202_09421_gb300 import binding as B
+    wl = _wl()
+    s = _tc_solver(wl)
+    B.rte_inject_fault(s.ctx, B.RTE_FAULT_TIMEOUT_WORD)
+    assert _status(s.forward, wl.groups, wl.n_steps) == TIMEOUT
+    state = torch.empty((wl.grid.ny, wl.grid.nx, wl.grid.M), dtype=torch.float32, device="cuda:0")
+    B.rte_get_state(s.ctx, 0, state)
+    assert float(state.abs().max()) == 0.0                        # no pass did any work
+    s.forward(wl.groups, wl.n_steps)
+    curves = s.readout(wl.detectors).cpu().numpy()
+    s.close()
+    assert rel_l2(curves[0], _oracle_curves(wl)) < 1e-5
+
+
+def test_expiring_device_wait_reports_timeout():
+    """One CTA of the first pass waits on a barrier that nothing arrives on
+    (before it issues any copy or MMA): the bounded wait runs out (about
+    2 s), the march reports TIMEOUT, and the context then solves correctly."""
+    from paper_2202_09421_gb300 import binding as B
+    wl = _wl()
+    s = _tc_solver(wl)
+    B.rte_set_pass_variant(s.ctx, 1)
+    B.rte_inject_fault(s.ctx, B.RTE_FAULT_EXPIRE_WAIT)
+    assert _status(s.forward, wl.groups, wl.n_steps) == TIMEOUT
+    s.forward(wl.groups, wl.n_steps)
+    curves = s.readout(wl.detectors).cpu().numpy()
+    s.close()
+    assert rel_l2(curves[0], _oracle_curves(wl)) < 1e-5
+
+
+def test_timeout_word_is_per_context():
+    """A timeout in one context leaves another context's march untouched."""
+    from paper_2202_09421_gb300 import binding as B
+    wl = _wl()
+    s1, s2 = _tc_solver(wl), _tc_solver(wl)
+    B.rte_inject_fault(s1.ctx, B.RTE_FAULT_TIMEOUT_WORD)
+    s2.forward(wl.groups, wl.n_steps)
+    curves = s2.readout(wl.detectors).cpu().numpy()
+    assert _status(s1.forward, wl.groups, wl.n_steps) == TIMEOUT
+    s1.close()
+    s2.close()
+    assert rel_l2(curves[0], _oracle_curves(wl)) < 1e-5
+
+
+def test_fault_injection_rejected_where_there_are_no_device_waits():
+    from paper_2202_09421_gb300 import binding as B
+    from paper_2202_09421_gb300.solver import FCDOMSolver
+    wl = _wl()
+    s = FCDOMSolver(wl.grid, wl.optics, _t(wl.mua), _t(wl.mus), wl.c, wl.dt)
+    assert _status(B.rte_inject_fault, s.ctx, B.RTE_FAULT_TIMEOUT_WORD) == UNSUPPORTED
+    s2 = _tc_solver(wl)
+    assert _status(B.rte_inject_fault, s2.ctx, 9) == INVALID_ARG
+    s.close()
+    s2.close()
