@@ -59,10 +59,6 @@ NCU_TRAFFIC = {
     # full on the tomography workload's per-launch size (16 groups x 256^2 x
     # 32), keyed by the kernel and the sha256 prefix of its sources; an entry
     # whose sources changed since its capture no longer matches.
-    # tcgen05 3xTF32 passes, one tile per CTA (csrc/rte_tc.cu + rte_tc_common.cuh):
-    # profiles/tc_passes_tomo256_ncu_full.md
-    ("tc_pass_kernel<x>", "855a828dbd9638c2"): 136.838144e6 + 83.234816e6,
-    ("tc_pass_kernel<y>", "855a828dbd9638c2"): 687.241728e6 + 192.933632e6,
     # tile-local fused step, 16 x 16 parts (csrc/rte_fused.cu):
     # profiles/fused_step_tomo256_ncu_full.md
     ("fused_step_kernel", "d911f8dcf7817a68"): 538.570240e6 + 231.271168e6,
@@ -120,26 +116,58 @@ def aggregate(updates_per_rank: int, local_ms: float, world: int, max_fn=None):
 
 
 # ---------------------------------------------------------------- oracle timing
-def oracle_rate(n_steps: int, threads: int = 1):
-    """Times the FP64 oracle on one source of the tomography workload for
-    n_steps AB4 steps in a fresh interpreter pinned to `threads` threads."""
-    code = (
-        "import sys,time,json; sys.path.insert(0, %r)\n"
-        "from rte_inputs import workload_tomo256\n"
-        "from oracle.rte import Solver\n"
-        "wl = workload_tomo256(n_steps=%d)\n"
-        "S = Solver(wl)\n"
-        "t = time.perf_counter(); S.forward(wl.groups[0], %d, wl.detectors); t = time.perf_counter() - t\n"
-        "g = wl.grid\n"
-        "print(json.dumps({'seconds': t, 'updates': g.nx * g.ny * g.M * %d}))\n"
-    ) % (ROOT, n_steps, n_steps, n_steps)
+_ORACLE_CHILD = """
+import json, os, sys, time
+sys.path.insert(0, %r)
+from rte_inputs import workload_tomo256
+from oracle.rte import Solver
+n_steps, src, gate = %d, int(sys.argv[1]), sys.argv[2]
+wl = workload_tomo256(n_steps=n_steps)
+S = Solver(wl)
+open(os.path.join(gate, "ready.%%d" %% src), "w").close()
+while not os.path.exists(os.path.join(gate, "go")):
+    time.sleep(0.001)
+t0 = time.time()
+S.forward(wl.groups[src %% len(wl.groups)], n_steps, wl.detectors)
+t1 = time.time()
+g = wl.grid
+print(json.dumps({"start": t0, "end": t1, "updates": g.nx * g.ny * g.M * n_steps}))
+"""
+
+
+def oracle_rate(n_steps: int, procs: int | None = None):
+    """Times the FP64 oracle on the machine's host cores: `procs` single-threaded
+    interpreters (default: one per host core), each solving one source of the
+    tomography workload (sources cycle over the 16) for n_steps AB4 steps.
+    The sources are independent forward solves, so they run side by side;
+    the oracle itself stays plain and single-threaded.  Every interpreter
+    sets up its solver, then all start together.  Returns (updates/s over
+    the wall time from the first start to the last end, that wall time in s,
+    procs)."""
+    procs = procs or os.cpu_count() or 1
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = str(threads)
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                         check=True)
-    r = json.loads(out.stdout.strip().splitlines()[-1])
-    return r["updates"] / r["seconds"], r["seconds"]
+        env[k] = "1"
+    code = _ORACLE_CHILD % (ROOT, n_steps)
+    with tempfile.TemporaryDirectory() as gate:
+        kids = [subprocess.Popen([sys.executable, "-c", code, str(k), gate], stdout=subprocess.PIPE,
+                                 stderr=subprocess.PIPE, text=True, env=env) for k in range(procs)]
+        deadline = time.time() + 600
+        while sum(os.path.exists(os.path.join(gate, f"ready.{k}")) for k in range(procs)) < procs:
+            if any(p.poll() not in (None, 0) for p in kids) or time.time() > deadline:
+                for p in kids:
+                    p.kill()
+                raise RuntimeError("oracle timing: an interpreter failed to start")
+            time.sleep(0.01)
+        open(os.path.join(gate, "go"), "w").close()
+        outs = []
+        for p in kids:
+            out, err = p.communicate()
+            if p.returncode != 0:
+                raise RuntimeError(f"oracle timing failed: {err[-500:]}")
+            outs.append(json.loads(out.strip().splitlines()[-1]))
+    wall = max(o["end"] for o in outs) - min(o["start"] for o in outs)
+    return sum(o["updates"] for o in outs) / wall, wall, procs
 
 
 def run_reference(args):
@@ -150,19 +178,21 @@ def run_reference(args):
     for _ in range(args.warmup):
         oracle_rate(max(2, n // 8))
     rates, secs = [], []
+    procs = 1
     for _ in range(args.steps):
-        r, s = oracle_rate(n)
+        r, sec, procs = oracle_rate(n)
         rates.append(r)
-        secs.append(s)
+        secs.append(sec)
     value = statistics.median(rates)
-    sample = f"1 of 16 sources x {n} AB4 steps of the tomography workload per step"
+    sample = (f"{procs} sources of the tomography workload side by side (one single-threaded FP64 oracle "
+              f"interpreter per host core, sources cycling over the 16) x {n} AB4 steps per step")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * statistics.median(secs), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -257,9 +287,11 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
-    def time_form(precision, steps, warmup, clocks=None, fc_parts=(1, 1), variant=None):
+    def time_form(precision, steps, warmup, fc_parts=(1, 1), variant=None, instrument=True):
         """Forward solve + detector readout per step; CUDA events on the
-        launching stream; L2 flushed before every timed step."""
+        launching stream; L2 flushed before every timed step.  The timed
+        steps run without the library's per-kernel events; one more step with
+        them on gives the per-pass times."""
         solver = FCDOMSolver(g, wl.optics, a, b, wl.c, wl.dt, ckpt_interval=0, precision=precision,
                              fc_parts=fc_parts)
         schedule = "one-tile" if args.no_autotune else args.schedule
@@ -284,7 +316,6 @@ def run_ours(args):
             flush.fill_(1.0)
         barrier()
         launches0 = solver.kernel_launches()
-        B.rte_set_kernel_timing(solver.ctx, True)
         times = []
         for k in range(steps):
             flush.fill_(float(k))                  # evict the previous step from L2
@@ -296,9 +327,18 @@ def run_ours(args):
             e1.record(stream)
             barrier()
             times.append(e0.elapsed_time(e1))
+        launches = solver.kernel_launches() - launches0
+        if not instrument:
+            return solver, statistics.mean(times), [0.0, 0.0], [0, 0], launches, one_step, tuned
+        # per-pass device times from one instrumented step (events on the
+        # library's stream around every pass), outside the timed region
+        flush.fill_(-1.0)
+        barrier()
+        B.rte_kernel_times(solver.ctx)
+        B.rte_set_kernel_timing(solver.ctx, True)
+        one_step()
         pass_ms, pass_cnt = B.rte_kernel_times(solver.ctx)
         B.rte_set_kernel_timing(solver.ctx, False)
-        launches = solver.kernel_launches() - launches0
         return solver, statistics.mean(times), pass_ms, pass_cnt, launches, one_step, tuned
 
     # Headline: tcgen05 tensor-core form with split 3xTF32 operands (FP32-level
@@ -308,39 +348,52 @@ def run_ours(args):
             B.RTE_PREC_TF32X3, args.steps, args.warmup)
     value, ms_step = aggregate(updates, ms_step, world, max_over_ranks)
 
-    # Roofline of the dominant pass.  y-pass: algorithmic 28 B per update
-    # (read u, R, L1..L3; write u, L) against HBM; x-pass: tensor-core flops
-    # (3 products x 2 flop x (n + M) per update) against the TF32 peak.
+    # Rooflines.  The step: the method's algorithmic 24 B per update (read
+    # u^k, L^{k-1..k-3}; write u^{k+1}, L^k) at the whole-step rate, against
+    # HBM.  The dominant pass: y-pass 28 B per update (read u, R, L1..L3;
+    # write u, L) against HBM; x-pass tensor-core flops (3 products x 2 flop
+    # x (n + M) per update) against the TF32 peak, and its 8 B per update
+    # against HBM.
     ncell_m = g.nx * g.ny * g.M * len(wl.groups)
+    step_gbs = 24.0 * updates / (ms_step / 1e3) / 1e9
     # the configuration timed: schedule = choice % 3 (0 persistent
     # warp-specialised, 1 one tile per CTA, 2 pipelined y-pass), choice >= 3
     # tensor-core scattering
     sched = tuned[0] % 3
     names = {0: ["tc_pass_ws<x>", "tc_pass_ws<y>"], 1: ["tc_pass_kernel<x>", "tc_pass_kernel<y>"],
              2: ["tc_pass_kernel<x>", "tc_ypass_pipe<y>"]}[sched]
-    dom = 0 if pass_ms[0] >= pass_ms[1] else 1
-    avg_ms = pass_ms[dom] / max(1, pass_cnt[dom])
-    if dom == 1:
-        achieved = 28.0 * ncell_m / (avg_ms / 1e3) / 1e9
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": PEAKS["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / PEAKS["hbm_gbs"], "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
-    else:
-        flops = 3 * 2 * (g.nx + g.M) * ncell_m
-        peak = PEAKS["bf16_tflops"] / 2.0
-        achieved = flops / (avg_ms / 1e3) / 1e12
-        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "peak_source": "measured bf16 burst x 1/2 (tf32 nominal ratio)"}
-    roofline.update({"traffic": NCU_TRAFFIC.get((names[dom], kernel_source_hash(names[dom]))),
-                     "kernel": names[dom],
-                     "pass_ms_per_launch": [pass_ms[0] / max(1, pass_cnt[0]), pass_ms[1] / max(1, pass_cnt[1])],
-                     "pass_share": [pass_ms[0] / sum(pass_ms), pass_ms[1] / sum(pass_ms)]})
+    per_launch = [pass_ms[k] / max(1, pass_cnt[k]) for k in range(2)]
+    x_gbs = 8.0 * ncell_m / (per_launch[0] / 1e3) / 1e9
+    x_tflops = 3 * 2 * (g.nx + g.M) * ncell_m / (per_launch[0] / 1e3) / 1e12
+    y_gbs = 28.0 * ncell_m / (per_launch[1] / 1e3) / 1e9
+    tf32_peak = PEAKS["bf16_tflops"] / 2.0
+    passes = {
+        names[0]: {"ms_per_launch": per_launch[0], "share": pass_ms[0] / sum(pass_ms),
+                   "hbm": {"achieved": x_gbs, "bytes_per_update": 8, "frac": x_gbs / PEAKS["hbm_gbs"]},
+                   "tensor": {"achieved": x_tflops, "unit": "TFLOP/s", "peak": tf32_peak,
+                              "frac": x_tflops / tf32_peak,
+                              "peak_source": "measured bf16 burst x 1/2 (tf32 nominal ratio)"},
+                   "traffic": NCU_TRAFFIC.get((names[0], kernel_source_hash(names[0])))},
+        names[1]: {"ms_per_launch": per_launch[1], "share": pass_ms[1] / sum(pass_ms),
+                   "hbm": {"achieved": y_gbs, "bytes_per_update": 28, "frac": y_gbs / PEAKS["hbm_gbs"]},
+                   "traffic": NCU_TRAFFIC.get((names[1], kernel_source_hash(names[1])))},
+    }
+    dom = 0 if per_launch[0] >= per_launch[1] else 1
+    dom_gbs = x_gbs if dom == 0 else y_gbs
+    roofline = {"step_frac": step_gbs / PEAKS["hbm_gbs"],
+                "step": {"bytes_per_update": 24, "achieved": step_gbs, "unit": "GB/s",
+                         "updates_per_s_ceiling": PEAKS["hbm_gbs"] * 1e9 / 24.0},
+                "bound": "hbm", "achieved": dom_gbs, "peak": PEAKS["hbm_gbs"], "unit": "GB/s",
+                "frac": dom_gbs / PEAKS["hbm_gbs"], "traffic": passes[names[dom]]["traffic"],
+                "kernel": names[dom], "peak_source": f"{PEAKS['source']} (MEASURED_PEAKS.json hbm_gbs)",
+                "passes": passes}
 
     # The other forms on the same workload: the plain FP32 SIMT form (the
     # metric's comparison) and the single-product TF32 reduced-precision form.
     forms = {}
     for name, prec, parts in (("plain_fp32_simt", B.RTE_PREC_FP32, (1, 1)), ("tf32_reduced", B.RTE_PREC_TF32, (1, 1)),
                               ("tf32x3_subdomains_4x4", B.RTE_PREC_TF32X3, (4, 4))):
-        s2, ms2, _, _, _, _, _ = time_form(prec, 1, 1, fc_parts=parts)
+        s2, ms2, _, _, _, _, _ = time_form(prec, 1, 1, fc_parts=parts, instrument=False)
         s2.close()
         ms2 = max_over_ranks(ms2)
         forms[name] = {"value": updates * world / (ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2,
@@ -361,7 +414,7 @@ def run_ours(args):
                      "frac": fused_gbs / PEAKS["hbm_gbs"], "kernel": "fused_step_kernel",
                      "ms_per_launch": k_ms,
                      "traffic": NCU_TRAFFIC.get(("fused_step_kernel", kernel_source_hash("fused_step_kernel")))}}
-    s2, ms2, _, _, _, _, _ = time_form(B.RTE_PREC_TF32X3, 1, 1, fc_parts=(16, 16), variant=1)
+    s2, ms2, _, _, _, _, _ = time_form(B.RTE_PREC_TF32X3, 1, 1, fc_parts=(16, 16), variant=1, instrument=False)
     s2.close()
     ms2 = max_over_ranks(ms2)
     forms["tf32x3_subdomains_16x16_two_pass"] = {"value": updates * world / (ms2 / 1e3), "unit": UNIT,
@@ -400,35 +453,38 @@ def run_ours(args):
         st.forward(tgt.groups, tgt.n_steps)
         measured = st.readout(tgt.detectors)
         st.close()
-        sa = FCDOMSolver(wm.grid, wm.optics, am, bm, wm.c, wm.dt, ckpt_interval=100,
-                         precision=B.RTE_PREC_TF32X3)
-        gt = []
-        for k in range(2):
-            flush.fill_(float(k))
-            barrier()
-            t0 = time.perf_counter()
-            sa.forward(wm.groups, wm.n_steps)
-            J, ga, gb = sa.adjoint_gradient(wm.detectors, measured)
-            torch.cuda.synchronize()
-            gt.append(time.perf_counter() - t0)
-        gs = max_over_ranks(gt[-1])
-        # the exact discrete adjoint (transposed march) on the same workload
-        dt_ = []
-        for k in range(2):
-            flush.fill_(float(k))
-            barrier()
-            t0 = time.perf_counter()
-            sa.forward(wm.groups, wm.n_steps)
-            J, ga, gb = sa.discrete_adjoint_gradient(wm.detectors, measured)
-            torch.cuda.synchronize()
-            dt_.append(time.perf_counter() - t0)
-        ds = max_over_ranks(dt_[-1])
+
+        def gradient_seconds(precision, discrete=False, reps=2):
+            """Wall time of one gradient (forward + checkpoint recompute +
+            adjoint march + gradient), the last of `reps` runs."""
+            sa = FCDOMSolver(wm.grid, wm.optics, am, bm, wm.c, wm.dt, ckpt_interval=100, precision=precision)
+            out = []
+            grads = None
+            for k in range(reps):
+                flush.fill_(float(k))
+                barrier()
+                t0 = time.perf_counter()
+                sa.forward(wm.groups, wm.n_steps)
+                fn = sa.discrete_adjoint_gradient if discrete else sa.adjoint_gradient
+                J, ga, gb = fn(wm.detectors, measured)
+                torch.cuda.synchronize()
+                out.append(time.perf_counter() - t0)
+                grads = (ga, gb)
+            sa.close()
+            return max_over_ranks(out[-1]), grads
+
+        gs, g_tc = gradient_seconds(B.RTE_PREC_TF32X3)
+        ds, _ = gradient_seconds(B.RTE_PREC_TF32X3, discrete=True)
+        fs, g_fp = gradient_seconds(B.RTE_PREC_FP32, reps=1)
         adjoint = {"gradients_per_s": world / gs, "seconds_per_gradient": gs,
+                   "plain_fp32_gradients_per_s": world / fs, "speedup_vs_plain_fp32": fs / gs,
+                   "dJ_dmua_rel_l2_vs_plain_fp32": _rel(g_tc[0], g_fp[0]),
+                   "dJ_dmus_rel_l2_vs_plain_fp32": _rel(g_tc[1], g_fp[1]),
                    "discrete_gradients_per_s": world / ds, "seconds_per_discrete_gradient": ds,
+                   "form": "tcgen05 3xTF32 (headline) against plain FP32 SIMT",
                    "workload": "mss256_M32: 256x256, M=32, 4 MSS groups x 4 beams, 3000 steps, "
                                "checkpoint every 100, 32 detectors",
                    "update_equivalents_per_gradient": 3 * wm.updates}
-        sa.close()
 
     configs = None
     if not args.no_configs:
@@ -439,10 +495,11 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, secs = oracle_rate(args.cpu_sample_steps)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"1 of 16 sources x {args.cpu_sample_steps} AB4 steps of the tomography "
-                         f"workload ({secs:.1f} s, FP64 numpy, 1 thread)"}
+        rate, secs, procs = oracle_rate(args.cpu_sample_steps + 20)
+        cpu = {"value": rate, "unit": UNIT, "cores": procs, "kind": "oracle",
+               "sample": f"{procs} sources of the tomography workload side by side (one single-threaded "
+                         f"FP64 oracle interpreter per host core) x {args.cpu_sample_steps + 20} AB4 steps "
+                         f"({secs:.1f} s wall)"}
 
     clocks = clk.summary()
     if rank == 0:
@@ -458,7 +515,7 @@ def run_ours(args):
                        "updates_per_step": updates * world, "l2": "flushed between timed steps "
                        "(256 MB write) and state > L2", "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks, "adjoint": adjoint, "forms": forms, "configs": configs, "inverse": inverse,
+            "clocks": clocks, "forms": forms, "configs": configs, "inverse": inverse, "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
