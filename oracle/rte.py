@@ -292,6 +292,24 @@ class Solver:
         """eq. (photondensity) with the trapezoid rule: sum_m w u_m."""
         return self.w * u.sum(axis=0)
 
+    def photon_balance(self, u):
+        """Terms of the photon balance that integrating eq. (RTE) over theta
+        and Omega gives (the scattering term integrates to zero by the
+        normalisation of Sec. 4.1): photons in the domain int Phi / c, the
+        absorption rate int a Phi, and the net outward flux through the
+        boundary int_{dOmega} int (theta . nu) u dtheta, with the trapezoid
+        rule in angle, over the nodes (node areas) and along each face.  The
+        time derivative of the first equals minus the sum of the other two;
+        the inflow of the sources enters the net flux with a negative sign."""
+        area = self.node_area()
+        phi = self.fluence(u)
+        photons = float(np.sum(area * phi)) / self.c
+        absorption = float(np.sum(area * self.a * phi))
+        flux = 0.0
+        for F, (jj, ii, wg) in enumerate(self.bt.face_nodes):
+            flux += float(np.sum(wg * ((self.w * self.bt.face_cos[F]) @ u[:, jj, ii])))
+        return photons, absorption, flux
+
     # --- forward march ---------------------------------------------------
     def forward(self, beams, n_steps, detectors=None, snap_steps=(),
                 keep_states=False, inflow=None, volume_source=None, init=None,

@@ -373,21 +373,36 @@ def test_photon_balance_with_fresnel_boundary():
                              t_s=6.0, sigma_t=2.0)
         S = rte.Solver(wl)
         out = S.forward(wl.groups[0], steps, keep_states=True)
-        area = S.node_area()
-        _, w, xi, eta = rte.ordinates(8)
-        N = np.array([np.sum(area * S.fluence(u)) / wl.c for u in out["states"]])
-        absn = np.array([np.sum(area * wl.mua * S.fluence(u)) for u in out["states"]])
-        flux = []
-        for u in out["states"]:
-            tot = 0.0
-            for F, (jj, ii, wg) in enumerate(S.bt.face_nodes):
-                tot += np.sum(wg * ((w * S.bt.face_cos[F]) @ u[:, jj, ii]))
-            flux.append(tot)
-        rate = -np.array(flux) - absn
+        N, absn, flux = (np.array(v) for v in zip(*(S.photon_balance(u) for u in out["states"])))
+        rate = -flux - absn
         lhs = N[-1] - N[0]
         rhs = np.trapezoid(rate, dx=dt)
         errs.append(abs(lhs - rhs) / np.abs(N).max())
     assert max(errs) < 2e-3, errs
+
+
+def test_photon_balance_terms_closed_forms():
+    """The balance terms on fields with closed-form integrals: a uniform
+    isotropic u = 1 holds int Phi / c = 2 pi |Omega| / c and absorbs
+    2 pi int a; its net boundary flux is zero (every face sees as much
+    outflow as inflow).  The field u_m(x, y) = max(0, cos theta_m) x / L
+    (photons moving in +x, growing along x) has no flux through the left
+    face (x = 0) and none through the bottom and top faces (the angular sum
+    of sin theta over the forward half-circle vanishes); through the right
+    face it carries L int_{-pi/2}^{pi/2} cos^2 = L pi / 2, which the
+    trapezoid rule on 64 ordinates gives exactly (cos^2 sums to M/2 over
+    the circle, half of it on the forward side)."""
+    n, M, L = 33, 64, 2.0
+    wl = workload_custom(n, n, M, 1, 0.01, L=L, mua=0.3, mus=10.0, heterogeneous=False)
+    S = rte.Solver(wl)
+    N, absn, flux = S.photon_balance(np.ones((M, n, n)))
+    assert abs(N - 2 * np.pi * L * L / wl.c) < 1e-12 * N
+    assert abs(absn - 2 * np.pi * 0.3 * L * L) < 1e-12 * absn
+    assert abs(flux) < 1e-12
+    theta, _, _, _ = rte.ordinates(M)
+    u = np.maximum(0.0, np.cos(theta))[:, None, None] * (S.X / L)[None, None, :] * np.ones((1, n, 1))
+    _, _, flux = S.photon_balance(u)
+    assert abs(flux - L * np.pi / 2) < 1e-12
 
 
 # ---------------------------------------------------------------- subdomains
