@@ -71,6 +71,8 @@ def kernel_source_hash(name="tc_pass_ws"):
         srcs = ["rte_tc_ws.cu", "rte_tc_common.cuh"]
     elif name.startswith("tc_ypass_pipe"):
         srcs = ["rte_tc_pipe.cu", "rte_tc_common.cuh"]
+    elif name.startswith("tc_xpass_stream"):
+        srcs = ["rte_tc_stream.cu", "rte_tc_common.cuh"]
     elif name.startswith("tc_pass"):
         srcs = ["rte_tc.cu", "rte_tc_common.cuh"]
     elif name.startswith("fused_step"):
@@ -94,10 +96,11 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=40)
-    ap.add_argument("--schedule", default="auto", choices=["auto", "one-tile", "persistent", "pipelined"],
+    ap.add_argument("--schedule", default="auto",
+                    choices=["auto", "one-tile", "persistent", "pipelined", "stream"],
                     help="tensor-core pass schedule: autotuned, one tile per CTA (the default "
-                         "configuration), persistent warp-specialised, or one-tile x-pass with the "
-                         "pipelined persistent y-pass")
+                         "configuration), persistent warp-specialised, one-tile x-pass with the "
+                         "pipelined persistent y-pass, or the TMA-fed persistent x-pass")
     ap.add_argument("--no-autotune", action="store_true", help="same as --schedule one-tile")
     ap.add_argument("--inverse", type=int, default=0, metavar="ITERS",
                     help="also run the inverse solver (Algorithm 2) for ITERS L-BFGS-B iterations, "
@@ -303,7 +306,7 @@ def run_ours(args):
         elif schedule == "auto":
             tuned = solver.autotune(wl.groups, 40)
         else:
-            variant = {"persistent": 0, "one-tile": 1, "pipelined": 2}[schedule]
+            variant = {"persistent": 0, "one-tile": 1, "pipelined": 2, "stream": 4}[schedule]
             B.rte_set_pass_variant(solver.ctx, variant)
             tuned = (variant, {})
 
@@ -356,12 +359,12 @@ def run_ours(args):
     # against HBM.
     ncell_m = g.nx * g.ny * g.M * len(wl.groups)
     step_gbs = 24.0 * updates / (ms_step / 1e3) / 1e9
-    # the configuration timed: schedule = choice % 3 (0 persistent
-    # warp-specialised, 1 one tile per CTA, 2 pipelined y-pass), choice >= 3
-    # tensor-core scattering
-    sched = tuned[0] % 3
+    # the configuration timed: schedule = choice % 5 (0 persistent
+    # warp-specialised, 1 one tile per CTA, 2 pipelined y-pass, 4 TMA-fed
+    # persistent x-pass), choice >= 5 tensor-core scattering
+    sched = tuned[0] % 5
     names = {0: ["tc_pass_ws<x>", "tc_pass_ws<y>"], 1: ["tc_pass_kernel<x>", "tc_pass_kernel<y>"],
-             2: ["tc_pass_kernel<x>", "tc_ypass_pipe<y>"]}[sched]
+             2: ["tc_pass_kernel<x>", "tc_ypass_pipe<y>"], 4: ["tc_xpass_stream", "tc_pass_kernel<y>"]}[sched]
     per_launch = [pass_ms[k] / max(1, pass_cnt[k]) for k in range(2)]
     x_gbs = 8.0 * ncell_m / (per_launch[0] / 1e3) / 1e9
     x_tflops = 3 * 2 * (g.nx + g.M) * ncell_m / (per_launch[0] / 1e3) / 1e12
@@ -510,8 +513,9 @@ def run_ours(args):
             "config": {"workload": WORKLOAD_DESC,
                        "form": "tcgen05 tensor cores, split 3xTF32 operands (FP32-level accuracy)",
                        "autotune": {"choice": tuned[0], "trial_ms_per_40_steps": tuned[1],
-                                    "choices": "choice % 3: 0 persistent warp-specialised, 1 one tile per "
-                                               "CTA, 2 pipelined y-pass; choice >= 3: tensor-core scattering"},
+                                    "choices": "choice % 5: 0 persistent warp-specialised, 1 one tile per "
+                                               "CTA, 2 pipelined y-pass, 4 TMA-fed persistent x-pass; "
+                                               "choice >= 5: tensor-core scattering"},
                        "updates_per_step": updates * world, "l2": "flushed between timed steps "
                        "(256 MB write) and state > L2", "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

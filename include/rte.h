@@ -102,6 +102,11 @@ typedef struct rte_optics {
  * context's stream by events, so the call stays asynchronous on that stream.
  * Off while per-kernel timing is on. */
 #define RTE_FLAG_CUDA_GRAPH 2
+/* RTE_FLAG_PHOTON_BALANCE makes rte_forward record, after every step, the
+ * terms of the photon balance of every group in FP64 on the device (read
+ * with rte_photon_balance).  One extra reduction launch per step, reading
+ * the state once. */
+#define RTE_FLAG_PHOTON_BALANCE 4
 /* fc_parts_x, fc_parts_y: the subdomain decomposition of Sec. 4.4 /
  * Algorithm 1 along each axis (0 or 1: one domain).  With P parts the n
  * points of a line are split into P owned ranges [k n / P, (k + 1) n / P);
@@ -243,6 +248,25 @@ rte_status rte_adjoint_gradient(rte_ctx* ctx, const rte_detector* dets, int n_de
 rte_status rte_discrete_adjoint_gradient(rte_ctx* ctx, const rte_detector* dets, int n_det,
                                          const float* measured, double* J_out,
                                          float* dJ_dmua, float* dJ_dmus);
+
+/* Photon balance of the last rte_forward (the context needs
+ * RTE_FLAG_PHOTON_BALANCE).  Integrating eq. (RTE) over theta and Omega (the
+ * scattering term integrates to zero by the normalisation of Sec. 4.1)
+ * gives d/dt int Phi / c = - int a Phi - (net outward boundary flux), with
+ * Phi of eq. (photondensity) and the incoming source entering the flux with
+ * a negative sign.  For every group g and step s the library records, for
+ * the post-boundary-condition state at t = (s + 4) dt, in FP64:
+ *   out[(g n_steps + s) 3 + 0] = sum_nodes A_node Phi / c   (photons)
+ *   out[(g n_steps + s) 3 + 1] = sum_nodes A_node a Phi     (absorption rate)
+ *   out[(g n_steps + s) 3 + 2] = sum_faces sum_face nodes w_face
+ *                                sum_m w (theta_m . nu) u_m (net outflux)
+ * with the trapezoid node areas A_node, the face trapezoid weights w_face
+ * (half at the face ends) and w = 2 pi / M.  The M ordinates of a node are
+ * added in FP32 and every sum above that in FP64, in a fixed order (the
+ * result does not depend on the schedule).  out: device double
+ * [group][step][3], caller-owned.  Errors: INVALID_ARG, STATE (no forward
+ * with the flag since the last forward, batched forward), CUDA. */
+rte_status rte_photon_balance(rte_ctx* ctx, double* out);
 
 /* Copies the current AB4 state of group g (u after the last step, FP32
  * [ny][nx][M]) into out (device).  Diagnostic; INVALID_ARG, STATE. */

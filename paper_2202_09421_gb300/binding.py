@@ -21,6 +21,7 @@ RTE_PREC_BF16X3 = 3    # tcgen05 kind::f16, BF16 operands split hi + lo (three p
 RTE_PREC_BF16 = 4      # tcgen05 kind::f16, one BF16 product
 RTE_FLAG_TC_SCATTER = 1  # x-pass scattering as a tcgen05 contraction
 RTE_FLAG_CUDA_GRAPH = 2  # forward march captured and replayed as a CUDA graph
+RTE_FLAG_PHOTON_BALANCE = 4  # record the FP64 photon-balance terms of every step
 
 
 class RteGrid(ctypes.Structure):
@@ -68,7 +69,7 @@ EXPORTS = ("rte_init_medium", "rte_set_medium", "rte_forward", "rte_detector_rea
            "rte_set_kernel_timing", "rte_kernel_times", "rte_forward_static", "rte_forward_batch",
            "rte_graph_captures", "rte_set_pass_variant", "rte_last_cuda_error",
            "rte_autotune", "rte_host_fc_operator_parts", "rte_discrete_adjoint_gradient",
-           "rte_host_bc_transpose", "rte_inject_fault")
+           "rte_host_bc_transpose", "rte_inject_fault", "rte_photon_balance")
 
 _lib = None
 
@@ -107,6 +108,7 @@ def library() -> ctypes.CDLL:
         "rte_graph_captures": [P],
         "rte_set_pass_variant": [P, c_int],
         "rte_inject_fault": [P, c_int],
+        "rte_photon_balance": [P, P],
         "rte_last_cuda_error": [],
         "rte_autotune": [P, POINTER(RteSourceGroup), c_int, c_int, POINTER(c_int), POINTER(ctypes.c_float)],
     }
@@ -220,10 +222,10 @@ def rte_autotune(ctx, groups, n_trial_steps: int):
     for k, bl in enumerate(groups):
         garr[k] = RteSourceGroup(ctypes.cast(beam_arrays[k], POINTER(RteBeam)), len(bl))
     choice = c_int()
-    ms = (ctypes.c_float * 6)(*([-1.0] * 6))
+    ms = (ctypes.c_float * 10)(*([-1.0] * 10))
     _check(library().rte_autotune(ctx, garr, len(groups), int(n_trial_steps), ctypes.byref(choice), ms),
            "rte_autotune")
-    return choice.value, {k: ms[k] for k in range(6) if ms[k] >= 0.0}
+    return choice.value, {k: ms[k] for k in range(10) if ms[k] >= 0.0}
 
 
 def rte_graph_captures(ctx) -> int:
@@ -258,6 +260,14 @@ def rte_discrete_adjoint_gradient(ctx, dets, measured, dJ_dmua=None, dJ_dmus=Non
                                                    _dev_ptr(dJ_dmua, "dJ_dmua"), _dev_ptr(dJ_dmus, "dJ_dmus")),
            "rte_discrete_adjoint_gradient")
     return J.value
+
+
+def rte_photon_balance(ctx, out):
+    """Photon-balance terms of the last forward (device float64 [group][step][3]:
+    photons int Phi / c, absorption int a Phi, net outward boundary flux)."""
+    if out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous():
+        raise ValueError("out must be a contiguous CUDA float64 tensor")
+    _check(library().rte_photon_balance(ctx, c_void_p(out.data_ptr())), "rte_photon_balance")
 
 
 def rte_get_state(ctx, group: int, out):

@@ -49,6 +49,11 @@ struct rte_ctx {
   // and the test-only request that the next march's first pass time out
   DevBuf err;
   bool inject_expire = false;
+  // photon balance of the last rte_forward (RTE_FLAG_PHOTON_BALANCE):
+  // [G][n_steps][3] FP64 terms, block partials, per-group tickets, and the
+  // FP64 cos / sin of the ordinates
+  DevBuf bal, bal_partial, bal_ticket, trig;
+  bool bal_valid = false;
   int x_variant = 1;               // pass kernels: 0 persistent warp-specialised, 1 one tile per CTA, 2 pipelined y-pass
   // state of the last forward
   int G = 0, n_steps = -1, kmax = 0;
@@ -243,7 +248,7 @@ double angdist(double a, double b) {
 rte_status march(rte_ctx* c, DevBuf& U, DevBuf& R, DevBuf* L, int& hl, int G, int s_begin,
                  int s_end, const rte_kern::BoundaryArgs& b, bool save_ckpt,
                  const std::vector<int>& snap_index, float* fluence_out,
-                 std::vector<float*>* seg_out) {
+                 std::vector<float*>* seg_out, double* balance_out = nullptr) {
   const rte_kern::StepArgs a = step_args(c, G);
   const size_t gbytes = static_cast<size_t>(G) * c->plane * sizeof(float);
   const int I = c->par.ckpt_interval;
@@ -293,6 +298,11 @@ rte_status march(rte_ctx* c, DevBuf& U, DevBuf& R, DevBuf* L, int& hl, int G, in
     if (seg_out)
       RTE_TRY(cuda_status(cudaMemcpyAsync((*seg_out)[s - s_begin], cur, gbytes,
                                           cudaMemcpyDeviceToDevice, c->stream)));
+    if (balance_out)
+      RTE_TRY(cuda_status(rte_kern::launch_balance(
+          cur, c->plane, c->nx, c->ny, c->M, G, F(c->mua), D(c->trig), c->dx, c->dy, 2.0 * kPi / c->M,
+          c->opt.c, D(c->bal_partial), static_cast<unsigned*>(c->bal_ticket.p), balance_out, s, c->n_steps,
+          c->stream, &c->launches)));
   }
   if (cur != F(U))
     RTE_TRY(cuda_status(cudaMemcpyAsync(U.p, cur, gbytes, cudaMemcpyDeviceToDevice, c->stream)));
@@ -425,6 +435,7 @@ rte_status prepare_forward(rte_ctx* c, const rte_source_group* groups, int n_gro
   c->kmax = kmax;
   c->G = G;
   c->n_steps = n_steps;
+  c->bal_valid = false;
 
   RTE_TRY(cuda_status(cudaMemsetAsync(c->U.p, 0, gbytes, c->stream)));
   for (int q = 0; q < 3; ++q) RTE_TRY(cuda_status(cudaMemsetAsync(c->L[q].p, 0, gbytes, c->stream)));
@@ -542,7 +553,7 @@ const char* rte_last_cuda_error(void) { return cudaGetErrorName(g_last_cuda_erro
 long long rte_graph_captures(const rte_ctx* ctx) { return ctx ? ctx->graph_captures : -1; }
 
 rte_status rte_set_pass_variant(rte_ctx* c, int variant) {
-  if (!c || variant < 0 || variant > 3) return RTE_ERR_INVALID_ARG;
+  if (!c || variant < 0 || variant > 4) return RTE_ERR_INVALID_ARG;
   c->x_variant = variant;
   return RTE_OK;
 }
@@ -557,19 +568,22 @@ rte_status rte_inject_fault(rte_ctx* c, int kind) {
 rte_status rte_autotune(rte_ctx* c, const rte_source_group* groups, int n_groups, int n_trial_steps,
                         int* choice_out, float* ms_out) {
   if (!c || !groups || n_groups <= 0 || n_trial_steps < 4 || !choice_out) return RTE_ERR_INVALID_ARG;
-  *choice_out = c->x_variant + ((c->par.flags & RTE_FLAG_TC_SCATTER) ? 3 : 0);
+  *choice_out = c->x_variant + ((c->par.flags & RTE_FLAG_TC_SCATTER) ? 5 : 0);
   if (c->tc_mode == 0) return RTE_OK;                     // one kernel family, nothing to choose
   rte_kern::StepArgs probe = step_args(c, n_groups);
+  // configurations: schedule (0, 1, 2, 4) + 5 x (tensor-core scattering)
   std::vector<int> cands;
-  for (int choice = 0; choice < 6; ++choice) {
-    const int variant = choice % 3;
-    const bool scat = choice >= 3;
+  for (int choice = 0; choice < 10; ++choice) {
+    const int variant = choice % 5;
+    const bool scat = choice >= 5;
+    if (variant == 3) continue;                           // the fused step: chosen with the decomposition
     if (scat && !rte_kern::tc_supported(c->nx, c->ny, c->M, c->tc_mode, RTE_FLAG_TC_SCATTER)) continue;
     probe.x_variant = variant;
     probe.tc_scatter = scat ? 1 : 0;
     // skip configurations that would fall back to another one
     if (variant == 0 && !rte_kern::tc_ws_supported(probe)) continue;
     if (variant == 2 && !rte_kern::tc_pipe_supported(probe)) continue;
+    if (variant == 4 && !rte_kern::tc_stream_supported(probe)) continue;
     cands.push_back(choice);
   }
   const int keep_variant = c->x_variant, keep_flags = c->par.flags;
@@ -582,9 +596,9 @@ rte_status rte_autotune(rte_ctx* c, const rte_source_group* groups, int n_groups
   int best_choice = -1;
   for (size_t k = 0; k < cands.size() && st == RTE_OK; ++k) {
     const int choice = cands[k];
-    c->x_variant = choice % 3;
-    c->par.flags = (keep_flags & ~RTE_FLAG_TC_SCATTER) | (choice >= 3 ? RTE_FLAG_TC_SCATTER : 0);
-    if (choice >= 3) st = ensure_phase_image(c);
+    c->x_variant = choice % 5;
+    c->par.flags = (keep_flags & ~RTE_FLAG_TC_SCATTER) | (choice >= 5 ? RTE_FLAG_TC_SCATTER : 0);
+    if (choice >= 5) st = ensure_phase_image(c);
     // one untimed forward, then a timed one
     if (st == RTE_OK) st = rte_forward(c, groups, n_groups, n_trial_steps, nullptr, 0, nullptr);
     if (st == RTE_OK) st = cuda_status(cudaEventRecord(e0, c->stream));
@@ -607,8 +621,8 @@ rte_status rte_autotune(rte_ctx* c, const rte_source_group* groups, int n_groups
     c->par.flags = keep_flags;
     return st != RTE_OK ? st : RTE_ERR_STATE;
   }
-  c->x_variant = best_choice % 3;
-  c->par.flags = (keep_flags & ~RTE_FLAG_TC_SCATTER) | (best_choice >= 3 ? RTE_FLAG_TC_SCATTER : 0);
+  c->x_variant = best_choice % 5;
+  c->par.flags = (keep_flags & ~RTE_FLAG_TC_SCATTER) | (best_choice >= 5 ? RTE_FLAG_TC_SCATTER : 0);
   *choice_out = best_choice;
   return RTE_OK;
 }
@@ -688,6 +702,10 @@ rte_status rte_destroy(rte_ctx* c) {
   for (DevBuf* b : all) release(*b);
   release(c->batch_tab);
   release(c->err);
+  release(c->bal);
+  release(c->bal_partial);
+  release(c->bal_ticket);
+  release(c->trig);
   for (cudaEvent_t e : c->events) cudaEventDestroy(e);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   for (cudaEvent_t e : c->gev)
@@ -725,7 +743,7 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
   if (g->nx > 512 || g->ny > 512 || g->M > 64) return RTE_ERR_UNSUPPORTED;
   if (!(g->xmax > g->xmin) || !(g->ymax > g->ymin)) return RTE_ERR_INVALID_ARG;
   if (!(p->dt > 0) || !(o->c > 0) || !(o->n_in > 0) || !(o->n_out > 0) || std::fabs(o->g) >= 1.0 ||
-      p->ckpt_interval < 0 || (p->flags & ~(RTE_FLAG_TC_SCATTER | RTE_FLAG_CUDA_GRAPH)) != 0 ||
+      p->ckpt_interval < 0 || (p->flags & ~(RTE_FLAG_TC_SCATTER | RTE_FLAG_CUDA_GRAPH | RTE_FLAG_PHOTON_BALANCE)) != 0 ||
       p->precision < RTE_PREC_FP32 || p->precision > RTE_PREC_BF16 || p->fc_parts_x < 0 || p->fc_parts_y < 0)
     return RTE_ERR_INVALID_ARG;
   if (p->precision != RTE_PREC_FP32 && !rte_kern::tc_supported(g->nx, g->ny, g->M, p->precision, p->flags))
@@ -817,7 +835,13 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
       double wy = (j == 0 || j == g->ny - 1) ? 0.5 * c->dy : c->dy;
       area[static_cast<size_t>(j) * g->nx + i] = static_cast<float>(wx * wy);
     }
+  std::vector<double> trig(2 * static_cast<size_t>(g->M));
+  for (int m = 0; m < g->M; ++m) {
+    trig[m] = std::cos(2.0 * kPi * m / g->M);
+    trig[g->M + m] = std::sin(2.0 * kPi * m / g->M);
+  }
   rte_status s = ensure(c->err, sizeof(int));
+  if (s == RTE_OK) s = upload(c->trig, trig, c->stream);
   if (s == RTE_OK) s = cuda_status(cudaMemsetAsync(c->err.p, 0, sizeof(int), c->stream));
   if (s == RTE_OK && c->tc_mode != 0 && (p->flags & RTE_FLAG_TC_SCATTER)) s = ensure_phase_image(c);
   if (s == RTE_OK) s = upload(c->PT, PTf, c->stream);
@@ -849,17 +873,32 @@ rte_status rte_forward(rte_ctx* c, const rte_source_group* groups, int n_groups,
     snap_index[snap_steps[k]] = k;
   }
   RTE_TRY(prepare_forward(c, groups, n_groups, n_steps));
+  double* balance = nullptr;
+  if (c->par.flags & RTE_FLAG_PHOTON_BALANCE) {
+    const int G = c->G;
+    RTE_TRY(ensure(c->bal, static_cast<size_t>(G) * n_steps * 3 * sizeof(double)));
+    RTE_TRY(ensure(c->bal_partial,
+                   static_cast<size_t>(G) * rte_kern::balance_blocks(c->nx, c->ny, c->M) * 3 * sizeof(double)));
+    RTE_TRY(ensure(c->bal_ticket, static_cast<size_t>(G) * sizeof(unsigned)));
+    RTE_TRY(cuda_status(cudaMemsetAsync(c->bal_ticket.p, 0, static_cast<size_t>(G) * sizeof(unsigned), c->stream)));
+    balance = D(c->bal);
+  }
   const rte_kern::BoundaryArgs b = forward_bargs(c);
   std::vector<unsigned long long> key;
   append_forward_key(c, key);
   key.push_back(key_ptr(fluence_out));
+  key.push_back(key_ptr(balance));
+  key.push_back(key_ptr(c->bal_partial.p));
   for (int k = 0; k < n_snaps; ++k) key.push_back(static_cast<unsigned long long>(snap_steps[k]));
   RTE_TRY(run_march(c, key, [&]() {
     int hl = 0;
-    return march(c, c->U, c->R, c->L, hl, c->G, 0, n_steps, b, true, snap_index, fluence_out, nullptr);
+    return march(c, c->U, c->R, c->L, hl, c->G, 0, n_steps, b, true, snap_index, fluence_out, nullptr,
+                 balance);
   }));
   c->hl = (2 * n_steps) % 3;
-  return tc_check(c);
+  const rte_status st = tc_check(c);
+  if (st == RTE_OK && balance) c->bal_valid = true;
+  return st;
 }
 
 rte_status rte_forward_batch(rte_ctx* const* ctxs, int n_ctx, const rte_source_group* const* groups,
@@ -973,6 +1012,13 @@ rte_status rte_get_state(rte_ctx* c, int group, float* out) {
   if (c->n_steps <= 0 || group >= c->G) return RTE_ERR_STATE;
   return cuda_status(cudaMemcpyAsync(out, F(c->U) + static_cast<size_t>(group) * c->plane,
                                      c->plane * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+}
+
+rte_status rte_photon_balance(rte_ctx* c, double* out) {
+  if (!c || !out) return RTE_ERR_INVALID_ARG;
+  if (!c->bal_valid) return RTE_ERR_STATE;
+  return cuda_status(cudaMemcpyAsync(out, c->bal.p, static_cast<size_t>(c->G) * c->n_steps * 3 * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, c->stream));
 }
 
 rte_status rte_objective(rte_ctx* c, const rte_detector* dets, int n_det, const float* measured,

@@ -454,6 +454,115 @@ __global__ void to_float_kernel(const double* in, float* out, size_t n) {
   if (k < n) out[k] = static_cast<float>(in[k]);
 }
 
+// Photon balance of one post-BC state (eq. RTE integrated over theta and
+// Omega; the scattering term integrates to zero): per group, the FP64 sums
+//   S0 = sum_nodes A_node sum_m u_m,   S1 = sum_nodes A_node a sum_m u_m,
+//   S2 = sum_faces sum_face nodes w_face sum_m (theta_m . nu) u_m,
+// with the trapezoid node areas A_node and face weights w_face (half at the
+// face ends).  One thread per float4 of the state: the M/4 lanes of a node
+// add its ordinates in FP32 (a pairwise tree of M terms) and the node's first
+// lane does the weighted FP64 accumulation; boundary nodes add their flux in
+// FP64 from a double table of cos and sin of the ordinates.  Each block
+// reduces a fixed range in a fixed order; the last block of a group to
+// finish (ticket counter) adds the block partials in block order, so the sums
+// do not depend on the schedule.  out[(g n_steps + step) 3 + k] =
+// (w S0 / c, w S1, w S2).
+constexpr int kBalThreads = 256, kBalItems = 8;
+
+__global__ void __launch_bounds__(kBalThreads)
+    balance_kernel(const float* __restrict__ U, size_t plane, int nx, int ny, int M,
+                   const float* __restrict__ mua, const double* __restrict__ trig, double dx, double dy,
+                   double w, double inv_c, double* __restrict__ partial, unsigned* __restrict__ ticket,
+                   double* __restrict__ out, int step, int n_steps) {
+  __shared__ double red[3][kBalThreads / 32];
+  __shared__ int last;
+  const int g = blockIdx.y, b = blockIdx.x, nb = gridDim.x;
+  const int V = M / 4;                                  // lanes per node: 2, 4, 8 or 16
+  const long long n4 = static_cast<long long>(nx) * ny * V;
+  const float4* u4 = reinterpret_cast<const float4*>(U + static_cast<size_t>(g) * plane);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  const long long base = static_cast<long long>(b) * kBalItems * kBalThreads;
+  for (int k = 0; k < kBalItems; ++k) {
+    const long long q = base + static_cast<long long>(k) * kBalThreads + threadIdx.x;
+    const bool valid = q < n4;                          // node groups never straddle the end
+    const float4 v = valid ? __ldcs(u4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float su = (v.x + v.y) + (v.z + v.w);
+    for (int o = 1; o < V; o <<= 1) su += __shfl_xor_sync(0xffffffffu, su, o);
+    if (!valid) continue;
+    const long long node = q / V;
+    const int r = static_cast<int>(q - node * V);
+    const int j = static_cast<int>(node / nx), i = static_cast<int>(node - static_cast<long long>(j) * nx);
+    const double wx = (i == 0 || i == nx - 1) ? 0.5 * dx : dx;
+    const double wy = (j == 0 || j == ny - 1) ? 0.5 * dy : dy;
+    if (r == 0) {
+      const double an = wx * wy * static_cast<double>(su);
+      s0 += an;
+      s1 += an * static_cast<double>(__ldg(mua + node));
+    }
+    if (i == 0 || i == nx - 1 || j == 0 || j == ny - 1) {
+      const int m0 = 4 * r;
+      const double e[4] = {v.x, v.y, v.z, v.w};
+      double fx = 0.0, fy = 0.0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        fx += __ldg(trig + m0 + t) * e[t];
+        fy += __ldg(trig + M + m0 + t) * e[t];
+      }
+      if (i == 0) s2 -= wy * fx;
+      if (i == nx - 1) s2 += wy * fx;
+      if (j == 0) s2 -= wx * fy;
+      if (j == ny - 1) s2 += wx * fy;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if (lane == 0) {
+    red[0][warp] = s0;
+    red[1][warp] = s1;
+    red[2][warp] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < 3; ++k)
+      for (int wv = 0; wv < kBalThreads / 32; ++wv) t[k] += red[k][wv];
+    double* pp = partial + (static_cast<size_t>(g) * nb + b) * 3;
+    pp[0] = t[0];
+    pp[1] = t[1];
+    pp[2] = t[2];
+    __threadfence();
+    last = atomicAdd(ticket + g, 1u) == static_cast<unsigned>(nb - 1);
+  }
+  __syncthreads();
+  if (!last || warp != 0) return;
+  // the group's last block: lane l adds blocks l, l + 32, ... in order, then
+  // a fixed butterfly combines the lanes
+  __threadfence();
+  const volatile double* pg = partial + static_cast<size_t>(g) * nb * 3;
+  double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+  for (int bb = lane; bb < nb; bb += 32) {
+    t0 += pg[3 * bb];
+    t1 += pg[3 * bb + 1];
+    t2 += pg[3 * bb + 2];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+    t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+    t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+  }
+  if (lane == 0) {
+    double* o = out + (static_cast<size_t>(g) * n_steps + step) * 3;
+    o[0] = w * inv_c * t0;
+    o[1] = w * t1;
+    o[2] = w * t2;
+    ticket[g] = 0u;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_step(const StepArgs& a, const BoundaryArgs& b, float* U, float* R,
@@ -526,6 +635,22 @@ cudaError_t launch_rho(const float* resid, const float* Wn, int n_det, int ring_
   if (total == 0) return cudaSuccess;
   rho_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(resid, Wn, n_det, ring_len,
                                                                          n_steps, G, scale, rho);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+int balance_blocks(int nx, int ny, int M) {
+  const long long n4 = static_cast<long long>(nx) * ny * (M / 4);
+  return static_cast<int>((n4 + kBalItems * kBalThreads - 1) / (kBalItems * kBalThreads));
+}
+
+cudaError_t launch_balance(const float* U, size_t plane, int nx, int ny, int M, int G, const float* mua,
+                           const double* trig, double dx, double dy, double w, double c, double* partial,
+                           unsigned* ticket, double* out, int step, int n_steps, cudaStream_t s,
+                           long long* launches) {
+  dim3 grid(balance_blocks(nx, ny, M), G);
+  balance_kernel<<<grid, kBalThreads, 0, s>>>(U, plane, nx, ny, M, mua, trig, dx, dy, w, 1.0 / c, partial,
+                                              ticket, out, step, n_steps);
   if (launches) *launches += 1;
   return cudaGetLastError();
 }

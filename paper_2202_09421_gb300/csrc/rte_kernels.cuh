@@ -58,7 +58,8 @@ struct StepArgs {
   // the split, pre-swizzled operators (tf32 words or bf16 halves).
   int tc_mode;
   int tc_scatter;                   // x-pass scattering as a tcgen05 contraction
-  int x_variant;                    // 0 persistent warp-specialised passes, 1 one tile per CTA, 2 pipelined y-pass
+  int x_variant;                    // 0 persistent warp-specialised passes, 1 one tile per CTA, 2 pipelined y-pass,
+                                    // 3 tile-local fused step, 4 TMA-fed persistent x-pass + one-tile y-pass
   const void* DxImg;
   const void* DyImg;
   const float* PImg;                // phase matrix as the scattering operand
@@ -136,6 +137,12 @@ bool tc_pipe_supported(const StepArgs& a);
 cudaError_t launch_ypass_pipe(const StepArgs& a, const BoundaryArgs& b, float* U, const float* R, const float* L1,
                               const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s);
 
+// Persistent TMA-fed x-pass (rte_tc_stream.cu): TF32 operand kinds, nx <=
+// 256, M in {16, 32}, without the tensor-core scattering flag; the raw slab
+// arrives by tensor copies and is split into operands by converter warps.
+bool tc_stream_supported(const StepArgs& a);
+cudaError_t launch_xpass_stream(const StepArgs& a, const float* U, float* R, cudaStream_t s);
+
 // Tile-local fused step (rte_fused.cu): one launch per step over the
 // subdomains of the decomposed operator (parts >= 2 on both axes, owned
 // ranges <= kFusedOwnMax, M in {16, 32}); reads u^k from Uin and writes
@@ -175,6 +182,16 @@ cudaError_t launch_grad(const float* MU, const float* Useg, const float* PT, con
                         int nx, int ny, int M, int G, size_t plane, size_t useg_group_stride,
                         double scale, int flip, double* grad_a, double* grad_b, cudaStream_t s,
                         long long* launches);
+
+// Photon-balance sums of the post-BC state U (every group) for one step:
+// out[(g n_steps + step) 3 + k] = (photons int Phi / c, absorption int a Phi,
+// net outward boundary flux) in FP64; partial holds G * balance_blocks(...)
+// * 3 doubles, ticket G zeroed counters (left zeroed).
+int balance_blocks(int nx, int ny, int M);
+cudaError_t launch_balance(const float* U, size_t plane, int nx, int ny, int M, int G, const float* mua,
+                           const double* trig, double dx, double dy, double w, double c, double* partial,
+                           unsigned* ticket, double* out, int step, int n_steps, cudaStream_t s,
+                           long long* launches);
 
 cudaError_t launch_to_float(const double* in, float* out, size_t n, cudaStream_t s,
                             long long* launches);

@@ -83,7 +83,7 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
   extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bars[4];   // full, done, p_full, scat_done
   __shared__ uint32_t tmem_slot;
-  __shared__ float pcs[kMaxM];                 // P~[k][0] (M = 64 epilogue)
+  __shared__ float pcs[kMaxM];                 // P~[k][0]: the x-pass scattering weights
   const int nx = a.nx, ny = a.ny;
   constexpr int M = MM;
   const int n = XPASS ? nx : ny;
@@ -107,7 +107,7 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
     for (int k = 0; k < 4; ++k) mbar_init(smem_u32(&bars[k]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (XPASS && MM == 64)
+  if (XPASS)
     for (int k = tid; k < M; k += kThreads) pcs[k] = __ldg(a.PT + k);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -406,11 +406,6 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
 #pragma unroll
         for (int k = 0; k < MM / 4; ++k) u4[k] = up[k];
       };
-      // Scattering weights p_k = P~[k][0]; P~[m][q] = p_{(m - q) mod M}
-      // (symmetric circulant), used by the FP32 form of the scattering sum.
-      float pc[MM];
-#pragma unroll
-      for (int k = 0; k < MM; ++k) pc[k] = SCAT_TC ? 0.f : __ldg(a.PT + k);
       load_pair(half, ucur, abcur, bcur);
       for (int p = half; p < n_pairs; p += 2) {
         int t, rc, i, j;
@@ -434,13 +429,7 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
             for (int k = 0; k < MM / 4; ++k) {
               uu[4 * k] = ucur[k].x; uu[4 * k + 1] = ucur[k].y; uu[4 * k + 2] = ucur[k].z; uu[4 * k + 3] = ucur[k].w;
             }
-#pragma unroll
-            for (int m = 0; m < MM; ++m) {
-              float sc = 0.f;
-#pragma unroll
-              for (int q = 0; q < MM; ++q) sc = fmaf(pc[(m - q + MM) % MM], uu[q], sc);
-              acc[m] = fmaf(bcur, sc, acc[m] - abcur * uu[m]);
-            }
+            xpass_node_rhs<MM>(acc, uu, pcs, abcur, bcur);
 #pragma unroll
             for (int k = 0; k < MM / 4; ++k)
               st_hint(reinterpret_cast<float*>(rp + k), make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]),
@@ -859,8 +848,12 @@ cudaError_t launch_step_tc(const StepArgs& a, const BoundaryArgs& b, float* U, f
   // the transposed step exists in the one-tile-per-CTA passes only
   const bool ws = a.x_variant == 0 && tc_ws_supported(a) && !b.bct_src;
   const bool pipe = a.x_variant == 2 && tc_pipe_supported(a) && !b.bct_src;
-  e = ws ? launch_pass_ws(true, a, b, U, R, L1, L2, L3, step, ring_step, s)
-         : launch_mode<true>(a, b, U, R, L1, L2, L3, step, ring_step, s);
+  // the TMA-fed x-pass (its scattering sum is the same as the one-tile
+  // x-pass's; the transposed step uses the one-tile passes throughout)
+  const bool stream = a.x_variant == 4 && tc_stream_supported(a) && !b.bct_src && !a.test_expire;
+  e = ws       ? launch_pass_ws(true, a, b, U, R, L1, L2, L3, step, ring_step, s)
+      : stream ? launch_xpass_stream(a, U, R, s)
+               : launch_mode<true>(a, b, U, R, L1, L2, L3, step, ring_step, s);
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[1], s);
   e = ws     ? launch_pass_ws(false, a, b, U, R, L1, L2, L3, step, ring_step, s)

@@ -170,6 +170,28 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
   for (int t = 0; t < 8; ++t) v[t] = __uint_as_float(r[t]);
 }
 
+// x-pass epilogue at one node (Sec. 4.1, eq. RTEAB4L): acc[m] holds the
+// streaming term -xi_m (D_x u)_m from the tensor cores; on return
+//   acc[m] = acc[m] - (a + b) u_m + sum_d p_d (b u_{(m - d) mod M}),
+// the circulant form of b P~u with p_d = P~[d][0] (P~[m][q] = p_{(m - q) mod M},
+// symmetric circulant).  The weights are read from shared memory, one
+// broadcast per d for all M outputs, so each d is M independent FMAs.
+// Overwrites uu with b u.
+template <int MM>
+__device__ __forceinline__ void xpass_node_rhs(float (&acc)[MM], float (&uu)[MM], const float* psm, float ab,
+                                               float bb) {
+#pragma unroll
+  for (int m = 0; m < MM; ++m) acc[m] = fmaf(-ab, uu[m], acc[m]);
+#pragma unroll
+  for (int m = 0; m < MM; ++m) uu[m] *= bb;
+#pragma unroll
+  for (int d = 0; d < MM; ++d) {
+    const float pd = psm[d];
+#pragma unroll
+    for (int m = 0; m < MM; ++m) acc[m] = fmaf(pd, uu[(m - d + MM) % MM], acc[m]);
+  }
+}
+
 struct TcLayout {
   int n, n_mt, n_kc, nrows_img, stage_bytes, tmem_cols;
   __host__ __device__ TcLayout(int n_, bool x3, int kc) : n(n_) {

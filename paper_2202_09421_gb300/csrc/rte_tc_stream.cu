@@ -1,0 +1,433 @@
+// Persistent, TMA-fed tcgen05 x-pass for sm_103a (lines of n <= 256
+// positions, M in {16, 32}, TF32 operand kinds: 3xTF32 and TF32).
+//
+// Same arithmetic as the x-pass of rte_tc.cu: for a slab tile of 128 columns
+// (grid rows j0 .. j0 + 128/M - 1 times the M ordinates) over a whole grid
+// row, acc[i][c] = sum_k D_x[i][k] (-xi_m u(c, k)) on the tensor cores (the
+// dense FC operator of Sec. 4.3), and R = b P~u - (a + b) u + acc in the
+// epilogue (Sec. 4.1, eq. RTEAB4L).  One CTA per SM walks its share of the
+// tiles; its roles run on separate warps and hand work over through
+// mbarriers:
+//   warp 12, one lane   the copy engine.  Per K chunk (32 positions) it
+//                       issues a tensor copy (cp.async.bulk.tensor over a 4D
+//                       map of the state [group][row][position][ordinate])
+//                       of the raw FP32 slab chunk, 128 slab columns x 32
+//                       positions, into a ring of raw buffers, and a bulk
+//                       copy of the split operator chunk (D hi, D lo, both
+//                       output tiles) into a ring of operand stages;
+//   warps 8-11          convert each raw chunk: scale by -xi_m, split into
+//                       TF32 hi + lo and write the K-major 128-byte-swizzle
+//                       operand of the same stage (each thread keeps one
+//                       slab column, so its scale is fixed);
+//   warp 13, one lane   issues the MMAs of each chunk into one of two
+//                       tensor-memory accumulators; the commit frees the
+//                       stage, the tile's last one hands the accumulator to
+//                       the epilogue;
+//   warps 0-7           drain the previous tile's accumulator: the FP32
+//                       circulant scattering sum, absorption, R to memory.
+// The slab never passes through registers on its way to the tensor cores,
+// and the operator copy, the conversion, the MMAs and the epilogue of
+// consecutive chunks and tiles overlap.
+// Every wait is bounded: on expiry the kernel raises the context's timeout
+// word and an abort flag that ends every other role's waits; the copy engine
+// waits for its copies in flight and the MMA lane for its MMAs before the
+// tensor memory is freed.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+
+#include "rte_tc_common.cuh"
+
+namespace rte_kern {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kEpiWarps = 8, kCvtWarps = 4;
+constexpr int kWarpCopy = kEpiWarps + kCvtWarps, kWarpMMA = kWarpCopy + 1;
+constexpr int kStThreads = (kWarpMMA + 1) * 32;
+constexpr int kCvtThreads = kCvtWarps * 32;
+constexpr int kMaxStages = 4, kRawStages = 2;
+constexpr int kSmemLimit = 232448 - 2048;
+constexpr int kChunkK = 32;                                   // K positions per chunk (TF32)
+constexpr int kRawBytes = kNC * kChunkK * 4;                  // raw FP32 chunk: 16 KB
+
+__device__ __forceinline__ bool st_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err) {
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try(bar, parity)) {
+    if (*abort_flag) return false;
+    if (global_ns() - t0 > kWaitNs) {
+      atomicExch(err, 1);
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+// Bounded wait without the abort check: the drains before the CTA leaves.
+__device__ __forceinline__ bool st_wait_plain(uint32_t bar, uint32_t parity, int* err) {
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try(bar, parity))
+    if (global_ns() - t0 > kWaitNs) {
+      atomicExch(err, 1);
+      return false;
+    }
+  return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Tensor copy of one box of a 4D map into shared memory, completing on bar.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+__host__ __device__ inline int stream_stages(int stage_bytes) {
+  const int s = (kSmemLimit - 1024 - kRawStages * kRawBytes) / stage_bytes;
+  return s > kMaxStages ? kMaxStages : s;
+}
+
+// 14 warps, one CTA per SM.  The register file is split over the four SM
+// sub-partitions, so with four warps on two of them a thread gets at most
+// 128 registers.
+template <int PREC, int MM>
+__global__ void __launch_bounds__(kStThreads, 1)
+    tc_xpass_stream(StepArgs a, const __grid_constant__ CUtensorMap umap, const float* __restrict__ U,
+                    float* __restrict__ R) {
+  using K = Kind<PREC>;
+  static_assert(!K::BF && K::KC == kChunkK, "TF32 operand kinds only");
+  constexpr bool X3 = K::X3;
+  constexpr int M = MM;
+  constexpr int per_tile = kNC / M;                 // grid rows per tile
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  // full_d[s], full_s[s], empty[s] (s < kMaxStages); raw_full[r],
+  // raw_empty[r] (r < kRawStages); acc_full[2], acc_empty[2]; mma_done
+  __shared__ __align__(8) uint64_t bars[3 * kMaxStages + 2 * kRawStages + 5];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  __shared__ float pweights[64];                    // P~[k][0], the x-pass scattering weights
+  const int nx = a.nx, ny = a.ny;
+  const TcLayout L(nx, X3, kChunkK);
+  const int S = stream_stages(L.stage_bytes);
+  const int tiles_per_group = (ny + per_tile - 1) / per_tile;
+  const int total = tiles_per_group * a.G;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // A launch after a timed-out one does nothing (the march reports the error).
+  if (*static_cast<volatile int*>(a.err)) return;
+  const int acc_cols = L.nrows_img;                 // one accumulator: n_mt * 128 columns
+  unsigned char* sm = smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023);
+  unsigned char* raw = sm + static_cast<size_t>(S) * L.stage_bytes;
+  auto bar = [&](int k) { return smem_u32(&bars[k]); };
+  auto full_d = [&](int s) { return bar(s); };
+  auto full_s = [&](int s) { return bar(kMaxStages + s); };
+  auto empty = [&](int s) { return bar(2 * kMaxStages + s); };
+  auto raw_full = [&](int r) { return bar(3 * kMaxStages + r); };
+  auto raw_empty = [&](int r) { return bar(3 * kMaxStages + kRawStages + r); };
+  auto acc_full = [&](int b2) { return bar(3 * kMaxStages + 2 * kRawStages + b2); };
+  auto acc_empty = [&](int b2) { return bar(3 * kMaxStages + 2 * kRawStages + 2 + b2); };
+  const uint32_t mma_done = bar(3 * kMaxStages + 2 * kRawStages + 4);
+
+  if (tid == 0) {
+    for (int s = 0; s < kMaxStages; ++s) {
+      mbar_init(full_d(s), 1);
+      mbar_init(full_s(s), kCvtThreads);
+      mbar_init(empty(s), 1);
+    }
+    for (int r = 0; r < kRawStages; ++r) {
+      mbar_init(raw_full(r), 1);
+      mbar_init(raw_empty(r), kCvtThreads);
+    }
+    for (int b2 = 0; b2 < 2; ++b2) {
+      mbar_init(acc_full(b2), 1);
+      mbar_init(acc_empty(b2), kEpiWarps * 32);
+    }
+    mbar_init(mma_done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int k = tid; k < MM; k += kStThreads) pweights[k] = __ldg(a.PT + k);
+  if (warp == kWarpCopy) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(2 * acc_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  volatile int* abrt = &abort_flag;
+  const int nrows_img = L.nrows_img;
+  const size_t chunk_bytes = static_cast<size_t>(2) * nrows_img * 128;
+  auto stage_ptr = [&](int s) { return sm + static_cast<size_t>(s) * L.stage_bytes; };
+
+  if (warp == kWarpCopy) {
+    // ---------------- copy engine ----------------
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&umap)) : "memory");
+      const unsigned char* Dimg = static_cast<const unsigned char*>(a.DxImg);
+      int n_raw = 0, n_op = 0;                      // copies issued into each ring
+      for (int tl = blockIdx.x; tl < total; tl += gridDim.x) {
+        const int g = tl / tiles_per_group, j0 = (tl - g * tiles_per_group) * per_tile;
+        for (int q = 0; q < L.n_kc; ++q) {
+          const int r = n_raw % kRawStages, s = n_op % S;
+          // the raw chunk first: the converters need it to fill the stage
+          if (!st_wait(raw_empty(r), ((n_raw / kRawStages) & 1) ^ 1, abrt, a.err)) goto copy_done;
+          tma_load_4d(smem_u32(raw + r * kRawBytes), &umap, 0, q * kChunkK, j0, g, raw_full(r), kRawBytes);
+          ++n_raw;
+          if (!st_wait(empty(s), ((n_op / S) & 1) ^ 1, abrt, a.err)) goto copy_done;
+          bulk_copy(smem_u32(stage_ptr(s)), Dimg + q * chunk_bytes, (X3 ? 2 : 1) * nrows_img * 128, full_d(s));
+          ++n_op;
+        }
+      }
+    copy_done:
+      // every copy issued has landed before the CTA leaves
+      for (int k = 0; k < kRawStages && k < n_raw; ++k) {
+        const int j = n_raw - 1 - k;
+        st_wait_plain(raw_full(j % kRawStages), (j / kRawStages) & 1, a.err);
+      }
+      for (int k = 0; k < S && k < n_op; ++k) {
+        const int j = n_op - 1 - k;
+        st_wait_plain(full_d(j % S), (j / S) & 1, a.err);
+      }
+    }
+  } else if (warp == kWarpMMA) {
+    // ---------------- MMA issue ----------------
+    if (lane == 0) {
+      // idesc: D = F32, A = B = TF32, K-major, M = 128 output positions,
+      // N = 128 slab columns.
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(kNC >> 3) << 17) |
+                             (static_cast<uint32_t>(kMT >> 4) << 24);
+      int it = 0, titer = 0;
+      for (int tl = blockIdx.x; tl < total; tl += gridDim.x, ++titer) {
+        const int b2 = titer & 1;
+        if (!st_wait(acc_empty(b2), ((titer >> 1) & 1) ^ 1, abrt, a.err)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        bool fine = true;
+        for (int q = 0; q < L.n_kc; ++q, ++it) {
+          const int s = it % S;
+          const uint32_t ph = (it / S) & 1;
+          if (!st_wait(full_d(s), ph, abrt, a.err) || !st_wait(full_s(s), ph, abrt, a.err)) {
+            fine = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          unsigned char* st = stage_ptr(s);
+          unsigned char* Dhi = st;
+          unsigned char* Dlo = st + L.n_mt * kTileBytes;
+          unsigned char* Shi = st + (X3 ? 2 : 1) * L.n_mt * kTileBytes;
+          unsigned char* Slo = Shi + kTileBytes;
+          const uint64_t dSh = sw128_desc(smem_u32(Shi)), dSl = sw128_desc(smem_u32(Slo));
+          for (int t = 0; t < L.n_mt; ++t) {
+            const uint64_t dDh = sw128_desc(smem_u32(Dhi + t * kTileBytes));
+            const uint64_t dDl = sw128_desc(smem_u32(Dlo + t * kTileBytes));
+            const uint32_t acc_t = tmem + b2 * acc_cols + t * kNC;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t o = static_cast<uint64_t>(kk * 2);   // 32 bytes per K step
+              mma<false>(acc_t, dDh + o, dSh + o, idesc, (q > 0 || kk > 0) ? 1u : 0u);
+              if (X3) {
+                mma<false>(acc_t, dDh + o, dSl + o, idesc, 1u);
+                mma<false>(acc_t, dDl + o, dSh + o, idesc, 1u);
+              }
+            }
+          }
+          mma_commit(empty(s));
+        }
+        if (!fine) break;
+        mma_commit(acc_full(b2));
+      }
+      // every MMA issued by this thread has completed before TMEM is freed
+      mma_commit(mma_done);
+      st_wait_plain(mma_done, 0, a.err);
+    }
+  } else if (warp >= kEpiWarps) {
+    // ---------------- conversion ----------------
+    // Thread ct owns slab column c = ct (grid row rc = c / M, ordinate m) and
+    // the 8 16-byte groups of 4 positions of its operand row.  Raw layout
+    // [rc][position][m]: a warp reads 32 consecutive words per position.
+    const int ct = tid - kEpiWarps * 32;
+    const int c = ct, rc = c / M, m = c - rc * M;
+    const float sc = -__ldg(a.xi + m);
+    int it = 0;
+    for (int tl = blockIdx.x; tl < total; tl += gridDim.x) {
+      bool fine = true;
+      for (int q = 0; q < L.n_kc; ++q, ++it) {
+        const int s = it % S, r = it % kRawStages;
+        if (!st_wait(raw_full(r), (it / kRawStages) & 1, abrt, a.err) ||
+            !st_wait(empty(s), ((it / S) & 1) ^ 1, abrt, a.err)) {
+          fine = false;
+          break;
+        }
+        const float* rw = reinterpret_cast<const float*>(raw + r * kRawBytes) + rc * kChunkK * M + m;
+        unsigned char* Shi = stage_ptr(s) + (X3 ? 2 : 1) * L.n_mt * kTileBytes;
+        unsigned char* Slo = Shi + kTileBytes;
+        float4 v[kChunkK / 4];
+#pragma unroll
+        for (int grp = 0; grp < kChunkK / 4; ++grp)
+          v[grp] = make_float4(rw[(4 * grp) * M], rw[(4 * grp + 1) * M], rw[(4 * grp + 2) * M], rw[(4 * grp + 3) * M]);
+        // The raw buffer is free once read.  The release of an mbarrier does
+        // not order these generic-proxy reads before the next tensor copy
+        // (async proxy) into the same buffer: without the proxy fence that
+        // copy can land before the reads are performed.
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(raw_empty(r));
+#pragma unroll
+        for (int grp = 0; grp < kChunkK / 4; ++grp) {
+          float4 hi, lo;
+          split4(v[grp], sc, hi, lo);
+          const int off = sw128_off(c, grp);
+          *reinterpret_cast<float4*>(Shi + off) = hi;
+          if (X3) *reinterpret_cast<float4*>(Slo + off) = lo;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(full_s(s));
+      }
+      if (!fine) break;
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    // lane = output position i, columns = (row, m).  Pairs (tile t, row rc)
+    // of the accumulator alternate between warps w and w + 4 (same quarter).
+    const int quarter = warp & 3, half = warp >> 2;
+    const int n_pairs = L.n_mt * per_tile;
+    // P~[m][q] = p_{(m - q) mod M}: the symmetric circulant's first column
+    // scattering weights p_k = P~[k][0], written before the CTA-wide barrier
+    // that precedes the roles
+    const float* pcs = pweights;
+    int titer = 0;
+    for (int tl = blockIdx.x; tl < total; tl += gridDim.x, ++titer) {
+      const int b2 = titer & 1;
+      if (!st_wait(acc_full(b2), (titer >> 1) & 1, abrt, a.err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int g = tl / tiles_per_group, t0 = (tl - g * tiles_per_group) * per_tile;
+      const size_t goff = static_cast<size_t>(g) * a.plane;
+      const uint32_t tq = tmem + (static_cast<uint32_t>(32 * quarter) << 16) + b2 * acc_cols;
+      for (int p = half; p < n_pairs; p += 2) {
+        const int t = p / per_tile, rc = p - t * per_tile;
+        const int i = t * kMT + 32 * quarter + lane, j = t0 + rc;
+        const bool valid = i < nx && j < ny;
+        const size_t cell = static_cast<size_t>(j) * nx + i;
+        float uu[MM];
+        float ab = 0.f, bb = 0.f;
+        if (valid) {
+          const float4* up = reinterpret_cast<const float4*>(U + goff + cell * M);
+#pragma unroll
+          for (int k = 0; k < MM / 4; ++k) {
+            const float4 u4 = __ldg(up + k);
+            uu[4 * k] = u4.x; uu[4 * k + 1] = u4.y; uu[4 * k + 2] = u4.z; uu[4 * k + 3] = u4.w;
+          }
+          bb = __ldg(a.mus + cell);
+          ab = __ldg(a.mua + cell) + bb;
+        } else {
+#pragma unroll
+          for (int k = 0; k < MM; ++k) uu[k] = 0.f;
+        }
+        float acc[MM];
+        tmem_ld16(tq + t * kNC + rc * M, acc);
+        if (MM > 16) tmem_ld16(tq + t * kNC + rc * M + 16, acc + 16);
+        if (valid) {
+          xpass_node_rhs<MM>(acc, uu, pcs, ab, bb);
+          float4* rp = reinterpret_cast<float4*>(R + goff + cell * M);
+#pragma unroll
+          for (int k = 0; k < MM / 4; ++k)
+            rp[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(acc_empty(b2));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == kWarpCopy)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * acc_cols));
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+template <int PREC, int MM>
+cudaError_t launch_stream_t(const StepArgs& a, const float* U, float* R, cudaStream_t s) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  // The state of all groups as a 4D tensor [G][ny][nx][M] (innermost first
+  // below); one box is one raw chunk: all M ordinates x 32 positions x the
+  // tile's rows of one group.  Positions past nx and rows past ny read as 0.
+  alignas(64) CUtensorMap map;
+  const cuuint64_t dims[4] = {static_cast<cuuint64_t>(MM), static_cast<cuuint64_t>(a.nx),
+                              static_cast<cuuint64_t>(a.ny), static_cast<cuuint64_t>(a.G)};
+  const cuuint64_t strides[3] = {static_cast<cuuint64_t>(MM) * 4, static_cast<cuuint64_t>(a.nx) * MM * 4,
+                                 static_cast<cuuint64_t>(a.plane) * 4};
+  const cuuint32_t box[4] = {static_cast<cuuint32_t>(MM), static_cast<cuuint32_t>(kChunkK),
+                             static_cast<cuuint32_t>(kNC / MM), 1u};
+  const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+  const CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(U), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  using K = Kind<PREC>;
+  const TcLayout L(a.nx, K::X3, kChunkK);
+  const int S = stream_stages(L.stage_bytes);
+  const size_t smem = 1024 + static_cast<size_t>(S) * L.stage_bytes + static_cast<size_t>(kRawStages) * kRawBytes;
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(tc_xpass_stream<PREC, MM>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  static int sm_count[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!sm_count[dev]) cudaDeviceGetAttribute(&sm_count[dev], cudaDevAttrMultiProcessorCount, dev);
+  const int sms = sm_count[dev] > 0 ? sm_count[dev] : 1;
+  const int tiles = (a.ny + kNC / MM - 1) / (kNC / MM) * a.G;
+  const int grid = tiles < sms ? tiles : sms;
+  tc_xpass_stream<PREC, MM><<<grid, kStThreads, smem, s>>>(a, map, U, R);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_stream_supported(const StepArgs& a) {
+  if (!(a.tc_mode == 1 || a.tc_mode == 2) || a.tc_scatter != 0 || a.nx > 256 || !(a.M == 16 || a.M == 32))
+    return false;
+  const TcLayout L(a.nx, a.tc_mode == 1, kChunkK);
+  return stream_stages(L.stage_bytes) >= 2;
+}
+
+cudaError_t launch_xpass_stream(const StepArgs& a, const float* U, float* R, cudaStream_t s) {
+  if (a.tc_mode == 1)
+    return a.M == 16 ? launch_stream_t<1, 16>(a, U, R, s) : launch_stream_t<1, 32>(a, U, R, s);
+  return a.M == 16 ? launch_stream_t<2, 16>(a, U, R, s) : launch_stream_t<2, 32>(a, U, R, s);
+}
+
+}  // namespace rte_kern

@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   __shared__ __align__(8) uint64_t bars[3 * kMaxStages + 5];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
+  __shared__ float pweights[64];                    // P~[k][0], the x-pass scattering weights
   const int nx = a.nx, ny = a.ny;
   const int n = XPASS ? nx : ny;              // line length (K and output positions)
   const int lines = XPASS ? ny : nx;          // grid rows (x) / columns (y)
@@ -149,6 +150,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       if (face) bc_wexit[e] = b.wexit[k];
     }
   }
+  if (XPASS)
+    for (int k = tid; k < MM; k += kWsThreads) pweights[k] = __ldg(a.PT + k);
   if (warp == kWarpD) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(2 * acc_cols));
@@ -332,9 +335,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     // of the accumulator alternate between warps w and w + 4 (same quarter).
     const int quarter = warp & 3, half = warp >> 2;
     const int n_pairs = L.n_mt * per_tile;
-    float pc[MM];
-#pragma unroll
-    for (int k = 0; k < MM; ++k) pc[k] = __ldg(a.PT + k);
+    // scattering weights p_k = P~[k][0], written before the CTA-wide barrier
+    // that precedes the roles
+    const float* pcs = pweights;
     int titer = 0;
     for (int tl = blockIdx.x; tl < total; tl += gridDim.x, ++titer) {
       const int b2 = titer & 1;
@@ -367,13 +370,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         tmem_ld16(tq + t * kNC + rc * M, acc);
         if (MM > 16) tmem_ld16(tq + t * kNC + rc * M + 16, acc + 16);
         if (valid) {
-#pragma unroll
-          for (int m = 0; m < MM; ++m) {
-            float sc = 0.f;
-#pragma unroll
-            for (int q = 0; q < MM; ++q) sc = fmaf(pc[(m - q + MM) % MM], uu[q], sc);
-            acc[m] = fmaf(bb, sc, acc[m] - ab * uu[m]);
-          }
+          xpass_node_rhs<MM>(acc, uu, pcs, ab, bb);
           float4* rp = reinterpret_cast<float4*>(R + goff + cell * M);
 #pragma unroll
           for (int k = 0; k < MM / 4; ++k) rp[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);

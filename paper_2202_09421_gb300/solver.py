@@ -68,6 +68,14 @@ class FCDOMSolver:
         J = B.rte_discrete_adjoint_gradient(self.ctx, detectors, measured.contiguous(), ga, gb)
         return J, ga, gb
 
+    def photon_balance(self) -> torch.Tensor:
+        """[group][step][3] float64: photons int Phi / c, absorption rate
+        int a Phi, net outward boundary flux of every step of the last
+        forward (the solver needs flags with RTE_FLAG_PHOTON_BALANCE)."""
+        out = torch.empty((self.n_groups, self.n_steps, 3), device=self.device, dtype=torch.float64)
+        B.rte_photon_balance(self.ctx, out)
+        return out
+
     def state(self, group: int) -> torch.Tensor:
         g = self.grid
         out = torch.empty((g.ny, g.nx, g.M), device=self.device, dtype=torch.float32)

@@ -199,9 +199,10 @@ def test_autotune_keeps_a_valid_configuration(precision):
     choice, ms = s.autotune(wl.groups, 12)
     print(f"autotune prec {precision}: choice {choice}, times {ms}")
     assert choice in ms and ms[choice] == min(ms.values())
-    # choice = schedule + 3 * TC scattering; the persistent warp-specialised
-    # schedule has no TC scattering, the BF16 kinds none at all
-    expected = {0, 1, 2, 4, 5} if precision == TF32X3 else {0, 1, 2}
+    # choice = schedule + 5 * TC scattering (schedules 0, 1, 2, 4); the
+    # persistent warp-specialised and the TMA-fed schedules have no TC
+    # scattering, the BF16 kinds none at all and no TMA-fed x-pass
+    expected = {0, 1, 2, 4, 6, 7} if precision == TF32X3 else {0, 1, 2}
     assert set(ms) == expected
     s.forward(wl.groups, wl.n_steps)
     curves = s.readout(wl.detectors).cpu().numpy()
@@ -233,3 +234,46 @@ def test_pipelined_ypass_matches_oracle(nx, ny, M, groups, precision):
     ec, ef = rel_l2(curves, c_ref), rel_l2(fl.cpu().numpy(), f_ref)
     print(f"pipelined y {nx}x{ny} M{M} prec {precision}: curves rel L2 {ec:.3e}, fluence rel L2 {ef:.3e}")
     assert ec <= TOL[precision] and ef <= TOL[precision]
+
+
+@pytest.mark.parametrize("nx,ny,M,groups", [(256, 256, 32, 3), (100, 70, 32, 2), (200, 131, 16, 1),
+                                            (45, 29, 16, 5), (256, 37, 16, 2)])
+@pytest.mark.parametrize("precision", [TF32X3, TF32])
+def test_tma_fed_xpass_matches_one_tile_bitwise(nx, ny, M, groups, precision):
+    """Schedule 4's x-pass (persistent, raw slab by tensor copies, converter
+    warps) issues the same splits, the same MMAs in the same order and the
+    same epilogue arithmetic as the one-tile x-pass, so the states after a
+    march are bit for bit the same; ragged sizes exercise the zero fill of
+    the tensor copies past the last row and position."""
+    from paper_2202_09421_gb300 import binding as B
+    from paper_2202_09421_gb300.solver import FCDOMSolver
+    wl = _stable_custom(nx, ny, M, groups, n_steps=30)
+    dev = torch.device("cuda:0")
+    states = []
+    for variant in (1, 4):
+        s = FCDOMSolver(wl.grid, wl.optics, torch.tensor(wl.mua, dtype=torch.float32, device=dev),
+                        torch.tensor(wl.mus, dtype=torch.float32, device=dev), wl.c, wl.dt, precision=precision)
+        B.rte_set_pass_variant(s.ctx, variant)
+        s.forward(wl.groups, wl.n_steps)
+        states.append([s.state(g).cpu().numpy() for g in range(groups)])
+        s.close()
+    for a_, b_ in zip(states[0], states[1]):
+        assert np.abs(a_).max() > 0
+        assert np.array_equal(a_, b_)
+
+
+def test_tma_fed_xpass_matches_oracle():
+    """Schedule 4 on a ragged multi-group case against the FP64 oracle (the
+    forward parity bound of the FP32-level forms)."""
+    from paper_2202_09421_gb300 import binding as B
+    from paper_2202_09421_gb300.solver import FCDOMSolver
+    wl = _stable_custom(100, 70, 32, 2)
+    dev = torch.device("cuda:0")
+    s = FCDOMSolver(wl.grid, wl.optics, torch.tensor(wl.mua, dtype=torch.float32, device=dev),
+                    torch.tensor(wl.mus, dtype=torch.float32, device=dev), wl.c, wl.dt, precision=TF32X3)
+    B.rte_set_pass_variant(s.ctx, 4)
+    s.forward(wl.groups, wl.n_steps, list(wl.snap_steps))
+    curves = s.readout(wl.detectors).cpu().numpy()
+    s.close()
+    ref, _, _ = oracle_forward(wl)
+    assert rel_l2(curves, ref) <= 1e-5, rel_l2(curves, ref)
