@@ -60,3 +60,37 @@ def test_autograd_function_backward_is_the_adjoint():
     assert abs(J.item() - J2) < 1e-12 * abs(J2)
     assert torch.allclose(a.grad, ga) and torch.allclose(b.grad, gb)
     s.close()
+
+
+def test_sharded_gradient_through_the_library_on_one_rank():
+    """sharded_gradient with the library's per-rank solve (a one-rank gloo
+    group): the shares and the FP64 all-reduce give the same J and gradient
+    as one rte_adjoint_gradient over all groups."""
+    import socket
+
+    import torch.distributed as dist
+
+    from paper_2202_09421_gb300.sharding import library_local_gradient, sharded_gradient
+    from paper_2202_09421_gb300.solver import FCDOMSolver
+    from rte_inputs import workload_custom
+    wl = workload_custom(40, 36, 16, 60, 0.04, L=1.0, mua=0.35, mus=8.0, n_groups=3, heterogeneous=False,
+                         t_s=1.0, sigma_t=0.4)
+    dev = torch.device("cuda:0")
+    meas = torch.zeros((3, len(wl.detectors), wl.n_steps), dtype=torch.float32, device=dev)
+    s = FCDOMSolver(wl.grid, wl.optics, torch.tensor(wl.mua, dtype=torch.float32, device=dev),
+                    torch.tensor(wl.mus, dtype=torch.float32, device=dev), wl.c, wl.dt, ckpt_interval=20)
+    s.forward(wl.groups, wl.n_steps)
+    J, ga, gb = s.adjoint_gradient(wl.detectors, meas)
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
+    try:
+        Js, gas, gbs = sharded_gradient(wl.groups, meas, library_local_gradient(s, wl.n_steps, wl.detectors),
+                                        (wl.grid.ny, wl.grid.nx))
+    finally:
+        dist.destroy_process_group()
+    s.close()
+    assert abs(Js - J) <= 1e-12 * abs(J)
+    assert np.array_equal(gas.numpy(), ga.double().cpu().numpy())
+    assert np.array_equal(gbs.numpy(), gb.double().cpu().numpy())
