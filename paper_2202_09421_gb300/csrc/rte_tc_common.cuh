@@ -159,6 +159,20 @@ __device__ __forceinline__ float ld_hint(const float* ptr, uint64_t pol) {
   return v;
 }
 
+// 32-byte global accesses (sm_100 and later): whole 32-byte sectors per
+// thread, so a warp that walks 32 nodes of 128 B leaves no half-written
+// sectors for L2 to merge.  Addresses are 32-byte aligned.
+__device__ __forceinline__ void ld8_nc(const float* ptr, float* v) {
+  asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "l"(ptr));
+}
+__device__ __forceinline__ void st8_hint(float* ptr, const float* v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8}, %9;" ::"l"(ptr), "f"(v[0]),
+               "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "l"(pol)
+               : "memory");
+}
+
 // 32 lanes x 8 columns of 32-bit words from tensor memory.
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
   uint32_t r[8];

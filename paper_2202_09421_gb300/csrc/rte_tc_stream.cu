@@ -305,6 +305,7 @@ __global__ void __launch_bounds__(kStThreads, 1)
     // scattering weights p_k = P~[k][0], written before the CTA-wide barrier
     // that precedes the roles
     const float* pcs = pweights;
+    const uint64_t pol_keep = policy_evict_last();
     int titer = 0;
     for (int tl = blockIdx.x; tl < total; tl += gridDim.x, ++titer) {
       const int b2 = titer & 1;
@@ -321,12 +322,8 @@ __global__ void __launch_bounds__(kStThreads, 1)
         float uu[MM];
         float ab = 0.f, bb = 0.f;
         if (valid) {
-          const float4* up = reinterpret_cast<const float4*>(U + goff + cell * M);
 #pragma unroll
-          for (int k = 0; k < MM / 4; ++k) {
-            const float4 u4 = __ldg(up + k);
-            uu[4 * k] = u4.x; uu[4 * k + 1] = u4.y; uu[4 * k + 2] = u4.z; uu[4 * k + 3] = u4.w;
-          }
+          for (int k = 0; k < MM / 8; ++k) ld8_nc(U + goff + cell * M + 8 * k, uu + 8 * k);
           bb = __ldg(a.mus + cell);
           ab = __ldg(a.mua + cell) + bb;
         } else {
@@ -338,10 +335,9 @@ __global__ void __launch_bounds__(kStThreads, 1)
         if (MM > 16) tmem_ld16(tq + t * kNC + rc * M + 16, acc + 16);
         if (valid) {
           xpass_node_rhs<MM>(acc, uu, pcs, ab, bb);
-          float4* rp = reinterpret_cast<float4*>(R + goff + cell * M);
+          // R is read by the y-pass that follows: keep it in L2
 #pragma unroll
-          for (int k = 0; k < MM / 4; ++k)
-            rp[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+          for (int k = 0; k < MM / 8; ++k) st8_hint(R + goff + cell * M + 8 * k, acc + 8 * k, pol_keep);
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
