@@ -262,6 +262,67 @@ __global__ void __launch_bounds__(kFThreads, 2)
 #pragma unroll
     for (int q = 0; q < MM; ++q) prow[q] = ps[m * MM + q];
     const int ring_len = 2 * ny + 2 * nx;
+    // An interior subdomain of the exact size has no node on the physical
+    // boundary, and its passes form a fixed grid (each warp's owned rows x the
+    // column passes), so every index below is a constant offset from the
+    // thread's bases.  Same arithmetic, in the same order, as the general
+    // loop that follows; the first batch's history (loaded before the
+    // derivatives) is for the same nodes.
+    const bool interior = EXACT && x_lo > 0 && x_hi < nx && y_lo > 0 && y_hi < ny;   // CTA-uniform
+    if (interior) {
+      constexpr int kRowsW = OM / kWarps;                        // owned rows per warp
+      constexpr int kColP = OM / kPerWarp;                       // column passes per row
+      constexpr int kPass = kRowsW * kColP;
+      const size_t hbase = goff + (static_cast<size_t>(y_lo + warp) * nx + x_lo + sub) * M + m;
+      const size_t hrow = static_cast<size_t>(kWarps) * nx * M;
+      auto hidx = [&](int pp) {
+        return hbase + static_cast<size_t>(pp / kColP) * hrow + static_cast<size_t>((pp % kColP) * kPerWarp) * M;
+      };
+      const float* unb = box + (warp + kHalo) * S::kRow + (sub + kHalo) * MM;
+#pragma unroll
+      for (int p0 = 0; p0 < kPass; p0 += kBatch) {
+        float g1[kBatch], g2[kBatch], g3[kBatch];
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t) {
+          const int pp = p0 + kBatch + t;
+          g1[t] = g2[t] = g3[t] = 0.f;
+          if (pp < kPass) {
+            const size_t e = hidx(pp);
+            g1[t] = __ldg(L1 + e);
+            g2[t] = __ldg(L2 + e);
+            g3[t] = L3[e];
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t) {
+          const int pp = p0 + t, rr = pp / kColP, cc = pp % kColP;
+          const float* un = unb + rr * kWarps * S::kRow + cc * kPerWarp * MM;
+          float2 s01 = make_float2(0.f, 0.f), s23 = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int q = 0; q < MM; q += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(un + q);
+            s01 = fma2(make_float2(prow[q], prow[q + 1]), make_float2(v.x, v.y), s01);
+            s23 = fma2(make_float2(prow[q + 2], prow[q + 3]), make_float2(v.z, v.w), s23);
+          }
+          const float sc = (s01.x + s01.y) + (s23.x + s23.y);
+          const float u = un[m];
+          const int n = (warp + kWarps * rr) * OM + sub + kPerWarp * cc;
+          const float av = abs_[n], bv = abs_[OM * OM + n];
+          const float lk = fmaf(bv, sc, lbuf[n * MM + m] - (av + bv) * u);
+          const float pre = fmaf(a.cdt, kAB0 * lk + kAB1 * h1[t] + kAB2 * h2[t] + kAB3 * h3[t], u);
+          const size_t e = hidx(pp);
+          L3[e] = lk;
+          Uout[e] = pre;
+        }
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t) {
+          h1[t] = g1[t];
+          h2[t] = g2[t];
+          h3[t] = g3[t];
+        }
+      }
+      return;
+    }
     int cj = warp, ci = sub;                         // compute cursor
     for (int t0 = 0; t0 < n_pass; t0 += kBatch) {
       float g1[kBatch], g2[kBatch], g3[kBatch];

@@ -455,19 +455,29 @@ __global__ void to_float_kernel(const double* in, float* out, size_t n) {
 }
 
 // Photon balance of one post-BC state (eq. RTE integrated over theta and
-// Omega; the scattering term integrates to zero): per group, the FP64 sums
+// Omega; the scattering term integrates to zero): per group,
 //   S0 = sum_nodes A_node sum_m u_m,   S1 = sum_nodes A_node a sum_m u_m,
 //   S2 = sum_faces sum_face nodes w_face sum_m (theta_m . nu) u_m,
 // with the trapezoid node areas A_node and face weights w_face (half at the
 // face ends).  One thread per float4 of the state: the M/4 lanes of a node
 // add its ordinates in FP32 (a pairwise tree of M terms) and the node's first
-// lane does the weighted FP64 accumulation; boundary nodes add their flux in
-// FP64 from a double table of cos and sin of the ordinates.  Each block
-// reduces a fixed range in a fixed order; the last block of a group to
-// finish (ticket counter) adds the block partials in block order, so the sums
-// do not depend on the schedule.  out[(g n_steps + step) 3 + k] =
-// (w S0 / c, w S1, w S2).
+// lane adds A_node sum_m u_m and a A_node sum_m u_m to its own compensated
+// (Kahan) FP32 sums, at most kBalItems nodes a thread; the boundary fluxes
+// are formed in FP64 from a double table of cos and sin of the ordinates.
+// GB300's FP64 pipe issues a warp instruction in tens of clocks, so FP64
+// work runs once per thread and per boundary node, not per node.  From the
+// threads up everything is FP64: warp and block sums in a fixed order, then
+// the last block of a group to finish (ticket counter) adds the block
+// partials in block order, so the sums do not depend on the schedule.
+// out[(g n_steps + step) 3 + k] = (w S0 / c, w S1, w S2).
 constexpr int kBalThreads = 256, kBalItems = 8;
+
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
+  const float y = x - comp;
+  const float t = sum + y;
+  comp = (t - sum) - y;
+  sum = t;
+}
 
 __global__ void __launch_bounds__(kBalThreads)
     balance_kernel(const float* __restrict__ U, size_t plane, int nx, int ny, int M,
@@ -478,29 +488,36 @@ __global__ void __launch_bounds__(kBalThreads)
   __shared__ int last;
   const int g = blockIdx.y, b = blockIdx.x, nb = gridDim.x;
   const int V = M / 4;                                  // lanes per node: 2, 4, 8 or 16
-  const long long n4 = static_cast<long long>(nx) * ny * V;
+  const int lv = __ffs(V) - 1;                          // log2 V
+  // at most 512 x 512 nodes x 16 float4: 32-bit indices
+  const int n4 = nx * ny * V;
   const float4* u4 = reinterpret_cast<const float4*>(U + static_cast<size_t>(g) * plane);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-  const long long base = static_cast<long long>(b) * kBalItems * kBalThreads;
+  const float fdx = static_cast<float>(dx), fdy = static_cast<float>(dy);
+  float a0 = 0.f, c0 = 0.f, a1 = 0.f, c1 = 0.f;        // Kahan sums of A sum_m u and a A sum_m u
+  double s2 = 0.0;
+  const int base = b * kBalItems * kBalThreads;
   for (int k = 0; k < kBalItems; ++k) {
-    const long long q = base + static_cast<long long>(k) * kBalThreads + threadIdx.x;
+    const int q = base + k * kBalThreads + static_cast<int>(threadIdx.x);
     const bool valid = q < n4;                          // node groups never straddle the end
     const float4 v = valid ? __ldcs(u4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
     float su = (v.x + v.y) + (v.z + v.w);
     for (int o = 1; o < V; o <<= 1) su += __shfl_xor_sync(0xffffffffu, su, o);
     if (!valid) continue;
-    const long long node = q / V;
-    const int r = static_cast<int>(q - node * V);
-    const int j = static_cast<int>(node / nx), i = static_cast<int>(node - static_cast<long long>(j) * nx);
-    const double wx = (i == 0 || i == nx - 1) ? 0.5 * dx : dx;
-    const double wy = (j == 0 || j == ny - 1) ? 0.5 * dy : dy;
+    const int node = q >> lv;
+    const int r = q & (V - 1);
+    const int j = node / nx, i = node - j * nx;
+    const bool xe = i == 0 || i == nx - 1, ye = j == 0 || j == ny - 1;
     if (r == 0) {
-      const double an = wx * wy * static_cast<double>(su);
-      s0 += an;
-      s1 += an * static_cast<double>(__ldg(mua + node));
+      // trapezoid node area: dx dy, halved on each face the node lies on
+      const float area = (xe ? 0.5f * fdx : fdx) * (ye ? 0.5f * fdy : fdy);
+      const float t = area * su;
+      kahan_add(a0, c0, t);
+      kahan_add(a1, c1, t * __ldg(mua + node));
     }
-    if (i == 0 || i == nx - 1 || j == 0 || j == ny - 1) {
+    if (xe || ye) {
+      const double wx = (i == 0 || i == nx - 1) ? 0.5 * dx : dx;
+      const double wy = (j == 0 || j == ny - 1) ? 0.5 * dy : dy;
       const int m0 = 4 * r;
       const double e[4] = {v.x, v.y, v.z, v.w};
       double fx = 0.0, fy = 0.0;
@@ -515,6 +532,8 @@ __global__ void __launch_bounds__(kBalThreads)
       if (j == ny - 1) s2 += wx * fy;
     }
   }
+  double s0 = static_cast<double>(a0) - static_cast<double>(c0);
+  double s1 = static_cast<double>(a1) - static_cast<double>(c1);
   for (int o = 16; o > 0; o >>= 1) {
     s0 += __shfl_xor_sync(0xffffffffu, s0, o);
     s1 += __shfl_xor_sync(0xffffffffu, s1, o);

@@ -36,7 +36,7 @@ def _run(s, wl):
 
 # (nx, ny, M, parts): owned ranges of 14..16 points, segments of 16..20;
 # ragged partitions (46 = 15 + 15 + 16, 45 = 15 x 3) and both kernel forms.
-CASES = [(48, 46, 16, (3, 3)), (64, 64, 32, (4, 4)), (45, 62, 32, (3, 4))]
+CASES = [(48, 46, 16, (3, 3)), (64, 64, 32, (4, 4)), (45, 62, 32, (3, 4)), (64, 64, 16, (4, 4)), (96, 80, 32, (6, 5))]
 
 
 @pytest.mark.parametrize("nx,ny,M,parts", CASES)
