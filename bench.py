@@ -55,13 +55,15 @@ PEAKS = load_peaks()
 # DRAM traffic per launch from an ncu capture, valid only for the kernel
 # source it was taken on.
 NCU_TRAFFIC = {
-    # dram__bytes_read.sum + dram__bytes_write.sum of one launch from ncu --set
-    # full on the tomography workload's per-launch size (16 groups x 256^2 x
-    # 32), keyed by the kernel and the sha256 prefix of its sources; an entry
+    # dram__bytes_read.sum + dram__bytes_write.sum of one launch from ncu on
+    # the tomography workload's per-launch size (16 groups x 256^2 x 32),
+    # keyed by the kernel and the sha256 prefix of its sources; an entry
     # whose sources changed since its capture no longer matches.
-    # tile-local fused step, 16 x 16 parts (csrc/rte_fused.cu):
-    # profiles/fused_step_tomo256_ncu_full.md
-    ("fused_step_kernel", "d911f8dcf7817a68"): 538.570240e6 + 231.271168e6,
+    # TMA-fed x-pass (csrc/rte_tc_stream.cu + rte_tc_common.cuh) and the
+    # one-tile y-pass (csrc/rte_tc.cu + rte_tc_common.cuh), schedule 4:
+    # profiles/tc_stream_passes_tomo256_ncu.md
+    ("tc_xpass_stream", "8a761a4512d9f193"): 135.925760e6 + 90.829568e6,
+    ("tc_pass_kernel<y>", "afb6b0b13f1a4d3e"): 689.004032e6 + 188.723456e6,
 }
 
 

@@ -462,7 +462,7 @@ __global__ void to_float_kernel(const double* in, float* out, size_t n) {
 // face ends).  One thread per float4 of the state: the M/4 lanes of a node
 // add its ordinates in FP32 (a pairwise tree of M terms) and the node's first
 // lane adds A_node sum_m u_m and a A_node sum_m u_m to its own compensated
-// (Kahan) FP32 sums, at most kBalItems nodes a thread; the boundary fluxes
+// (Kahan) FP32 sums, at most kBalItems nodes a thread (32); the boundary fluxes
 // are formed in FP64 from a double table of cos and sin of the ordinates.
 // GB300's FP64 pipe issues a warp instruction in tens of clocks, so FP64
 // work runs once per thread and per boundary node, not per node.  From the
@@ -470,7 +470,7 @@ __global__ void to_float_kernel(const double* in, float* out, size_t n) {
 // the last block of a group to finish (ticket counter) adds the block
 // partials in block order, so the sums do not depend on the schedule.
 // out[(g n_steps + step) 3 + k] = (w S0 / c, w S1, w S2).
-constexpr int kBalThreads = 256, kBalItems = 8;
+constexpr int kBalThreads = 256, kBalItems = 32;
 
 __device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
   const float y = x - comp;
