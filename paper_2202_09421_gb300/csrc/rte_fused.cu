@@ -49,7 +49,7 @@ __device__ __forceinline__ void cp16(float* dst, const float* src) {
 
 // Shared-memory layout (floats) of one CTA for MM ordinates and at most OM
 // owned points per axis; every region starts on a 16-byte boundary.  About
-// 92 KB at M = 32: two CTAs per SM.
+// 88 KB at M = 32: two CTAs per SM.
 template <int MM, int OM>
 struct FusedSmem {
   static constexpr int kBox = OM + 2 * kHalo;                      // box side (nodes)
@@ -57,7 +57,7 @@ struct FusedSmem {
   static constexpr int kOwn = OM * OM * MM;                        // owned values
   static constexpr int kBoxF = kBox * kRow;
   static constexpr int kOpF = (OM + 2 * kHalo) * OM;               // [k < seg][i < OM]
-  static constexpr int kTotal = kBoxF + kOwn + 2 * kOpF + MM * MM + 2 * OM * OM;
+  static constexpr int kTotal = kBoxF + kOwn + 2 * kOpF + 2 * OM * OM;
   static constexpr size_t kBytes = static_cast<size_t>(kTotal) * sizeof(float);
 };
 
@@ -87,8 +87,7 @@ __global__ void __launch_bounds__(kFThreads, 2)
   float* lbuf = box + S::kBoxF;                     // [ny_own][nx_own][MM]
   float* dxs = lbuf + S::kOwn;                      // [k < sx][i < OM]
   float* dys = dxs + S::kOpF;                       // [k < sy][j < OM]
-  float* ps = dys + S::kOpF;                        // [m][q] = P~[m][q]
-  float* abs_ = ps + MM * MM;                       // [2][ny_own][nx_own]: a, b
+  float* abs_ = dys + S::kOpF;                      // [2][ny_own][nx_own]: a, b
 
   const int nx = a.nx, ny = a.ny, M = MM;
   const int part = blockIdx.x, g = blockIdx.y;
@@ -157,10 +156,6 @@ __global__ void __launch_bounds__(kFThreads, 2)
       dxs[e] = __ldg(fx + e);
       dys[e] = __ldg(fy + e);
     }
-    for (int e = tid; e < MM * MM; e += kFThreads) {
-      const int mm = e / MM, q = e - mm * MM;
-      ps[e] = __ldg(a.PT + q * MM + mm);
-    }
     for (int e = tid; e < own; e += kFThreads) {
       const int jl = e / ox, il = e - jl * ox;
       const size_t cell = static_cast<size_t>(y_lo + jl) * nx + x_lo + il;
@@ -183,7 +178,11 @@ __global__ void __launch_bounds__(kFThreads, 2)
       float2 acc0[OM / 2], acc1[OM / 2];
 #pragma unroll
       for (int i = 0; i < OM / 2; ++i) acc0[i] = acc1[i] = make_float2(0.f, 0.f);
-      for (int k = 0; k < sx; ++k) {
+      // interior parts have the full segment (owned range + two fringe
+      // points on each side): a fixed trip count
+      const int kx_n = (EXACT && sx == OM + 2 * kHalo) ? OM + 2 * kHalo : sx;
+#pragma unroll 4
+      for (int k = 0; k < kx_n; ++k) {
         const float u0 = r0[k * MM], u1 = r1[k * MM];
         const float2 uu0 = make_float2(u0, u0), uu1 = make_float2(u1, u1);
         const float4* dk = reinterpret_cast<const float4*>(dxs + k * OM);
@@ -225,7 +224,9 @@ __global__ void __launch_bounds__(kFThreads, 2)
       float2 acc0[OM / 2], acc1[OM / 2];
 #pragma unroll
       for (int j = 0; j < OM / 2; ++j) acc0[j] = acc1[j] = make_float2(0.f, 0.f);
-      for (int k = 0; k < sy; ++k) {
+      const int ky_n = (EXACT && sy == OM + 2 * kHalo) ? OM + 2 * kHalo : sy;
+#pragma unroll 4
+      for (int k = 0; k < ky_n; ++k) {
         const float u0 = c0[k * S::kRow], u1 = c1[k * S::kRow];
         const float2 uu0 = make_float2(u0, u0), uu1 = make_float2(u1, u1);
         const float4* dk = reinterpret_cast<const float4*>(dys + k * OM);
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(kFThreads, 2)
   {
     float prow[MM];
 #pragma unroll
-    for (int q = 0; q < MM; ++q) prow[q] = ps[m * MM + q];
+    for (int q = 0; q < MM; ++q) prow[q] = __ldg(a.PT + q * MM + m);   // P~[m][q]: lanes read consecutive words
     const int ring_len = 2 * ny + 2 * nx;
     // An interior subdomain of the exact size has no node on the physical
     // boundary, and its passes form a fixed grid (each warp's owned rows x the
