@@ -615,8 +615,46 @@ def measure_batched(args, dev, flush, barrier, max_over_ranks, world):
     base = out["plain_fp32_per_medium"]["value"]
     for v in out.values():
         v["speedup_vs_plain_fp32"] = v["value"] / base
+
+    # Gradients of all 48 media (forward + checkpoint recompute + continuous
+    # adjoint, 3xTF32, checkpoints every 50 steps), data a 10 % weaker
+    # signal: the batched adjoint (one launch per pass over all media)
+    # against each medium's own adjoint after the same batched forward.
+    from paper_2202_09421_gb300.solver import adjoint_gradient_batch
+    ss = [FCDOMSolver(w.grid, w.optics, a, b, w.c, w.dt, precision=B.RTE_PREC_TF32X3, ckpt_interval=50)
+          for w, (a, b) in zip(wls, meds)]
+    forward_batch(ss, [w.groups for w in wls], n_steps)
+    meas = [0.9 * s_.readout(w.detectors) for s_, w in zip(ss, wls)]
+    dets = [w.detectors for w in wls]
+
+    def grad_batched():
+        forward_batch(ss, [w.groups for w in wls], n_steps)
+        return adjoint_gradient_batch(ss, dets, meas)
+
+    def grad_each():
+        forward_batch(ss, [w.groups for w in wls], n_steps)
+        return [s_.adjoint_gradient(w.detectors, m) for s_, w, m in zip(ss, wls, meas)]
+
+    grads = {}
+    for name, fn in (("batched", grad_batched), ("each_medium", grad_each)):
+        flush.fill_(0.0)
+        barrier()
+        t0 = time.perf_counter()
+        res = fn()
+        torch.cuda.synchronize()
+        grads[name] = (max_over_ranks(time.perf_counter() - t0), res)
+    dmax = max(float((x[1] - y[1]).abs().max()) for x, y in zip(grads["batched"][1], grads["each_medium"][1]))
+    for s_ in ss:
+        s_.close()
+    gradients = {"form": "tcgen05 3xTF32, checkpoints every 50 steps",
+                 "batched_gradient_sets_per_s": world / grads["batched"][0],
+                 "each_medium_gradient_sets_per_s": world / grads["each_medium"][0],
+                 "speedup": grads["each_medium"][0] / grads["batched"][0],
+                 "max_abs_diff_dJ_dmua_batched_vs_each": dmax,
+                 "unit": "gradient sets (all 48 media) per s"}
     return {"workload": "48 neck-like media, grids from {128,192,256,384}^2 at dx = 4/255 cm, M = 32, "
-                        f"one beam each, {n_steps} steps", "updates_per_solve_set": updates, "forms": out}
+                        f"one beam each, {n_steps} steps", "updates_per_solve_set": updates, "forms": out,
+            "gradients": gradients}
 
 
 def measure_precision512(args, dev, flush, barrier, max_over_ranks, world):

@@ -229,6 +229,29 @@ rte_status rte_adjoint_gradient(rte_ctx* ctx, const rte_detector* dets, int n_de
                                 const float* measured, double* J_out,
                                 float* dJ_dmua, float* dJ_dmus);
 
+/* Batched continuous adjoint: for n_ctx contexts whose last forward had the
+ * same step count (rte_forward_batch, or each its own rte_forward), with the
+ * same M, precision, flags, stream and checkpoint interval, computes for
+ * each context i what rte_adjoint_gradient computes: J_out[i] (host double,
+ * this call synchronises the stream) and the gradients dJ_dmua[i],
+ * dJ_dmus[i] (device FP32 [ny_i][nx_i]; the arrays, or their entries, may be
+ * NULL), from dets[i] (n_det[i] detectors) and measured[i] (device FP32
+ * [group][det][step]).  No counterpart in the paper beyond its independent
+ * forward/adjoint pairs per source (Sec. 3.4); batching fills the GPU with
+ * small media.  In the tensor-core precisions the media march in lockstep:
+ * each recomputed forward step and each adjoint step of eq.
+ * (AdjointProblem) is one x-pass and one y-pass launch over the tiles of all
+ * media, and each level's gradient terms (eq. FDwin22) and state saves are
+ * one launch each.  Segments are recomputed before their adjoint steps, not
+ * overlapped with them.  Each medium's results equal its own
+ * rte_adjoint_gradient.  In RTE_PREC_FP32 the media run one after another.
+ * Errors: INVALID_ARG (also mixed M, precision, flags, stream, step count or
+ * checkpoint interval, a repeated context, more than 64 contexts), STATE (no
+ * forward, or ckpt_interval == 0), OOM, CUDA, TIMEOUT. */
+rte_status rte_adjoint_gradient_batch(rte_ctx* const* ctxs, int n_ctx, const rte_detector* const* dets,
+                                      const int* n_det, const float* const* measured, double* J_out,
+                                      float* const* dJ_dmua, float* const* dJ_dmus);
+
 /* Objective and the exact gradient of the discrete objective: the same J as
  * rte_adjoint_gradient, and dJ/dmua, dJ/dmus with respect to the nodal values
  * of a and b of the discrete march itself (AB4 of eq. RTEAB4, the boundary

@@ -69,7 +69,7 @@ EXPORTS = ("rte_init_medium", "rte_set_medium", "rte_forward", "rte_detector_rea
            "rte_set_kernel_timing", "rte_kernel_times", "rte_forward_static", "rte_forward_batch",
            "rte_graph_captures", "rte_set_pass_variant", "rte_last_cuda_error",
            "rte_autotune", "rte_host_fc_operator_parts", "rte_discrete_adjoint_gradient",
-           "rte_host_bc_transpose", "rte_inject_fault", "rte_photon_balance")
+           "rte_host_bc_transpose", "rte_inject_fault", "rte_photon_balance", "rte_adjoint_gradient_batch")
 
 _lib = None
 
@@ -109,6 +109,8 @@ def library() -> ctypes.CDLL:
         "rte_set_pass_variant": [P, c_int],
         "rte_inject_fault": [P, c_int],
         "rte_photon_balance": [P, P],
+        "rte_adjoint_gradient_batch": [POINTER(c_void_p), c_int, POINTER(POINTER(RteDetector)), POINTER(c_int),
+                                       POINTER(c_void_p), POINTER(c_double), POINTER(c_void_p), POINTER(c_void_p)],
         "rte_last_cuda_error": [],
         "rte_autotune": [P, POINTER(RteSourceGroup), c_int, c_int, POINTER(c_int), POINTER(ctypes.c_float)],
     }
@@ -209,6 +211,27 @@ def rte_forward_batch(ctxs, groups_per_ctx, n_steps: int):
         ngr[i] = len(groups)
     carr = (c_void_p * n)(*[c.value for c in ctxs])
     _check(library().rte_forward_batch(carr, n, garrs, ngr, int(n_steps)), "rte_forward_batch")
+
+
+def rte_adjoint_gradient_batch(ctxs, dets_per_ctx, measured_per_ctx, dJ_dmua=None, dJ_dmus=None):
+    """Batched continuous adjoint over contexts that marched the same steps:
+    J per context (list of float); the gradients are written into the given
+    per-context device tensors (lists, entries may be None)."""
+    n = len(ctxs)
+    det_arrays = [make_detectors(d) for d in dets_per_ctx]
+    darr = (POINTER(RteDetector) * n)(*[ctypes.cast(a, POINTER(RteDetector)) for a in det_arrays])
+    ndet = (c_int * n)(*[len(d) for d in dets_per_ctx])
+    meas = (c_void_p * n)(*[_dev_ptr(m, "measured").value for m in measured_per_ctx])
+    J = (c_double * n)()
+
+    def ptrs(lst, name):
+        if lst is None:
+            return None
+        return (c_void_p * n)(*[(_dev_ptr(t, name).value if t is not None else None) for t in lst])
+    ga, gb = ptrs(dJ_dmua, "dJ_dmua"), ptrs(dJ_dmus, "dJ_dmus")
+    carr = (c_void_p * n)(*[c.value for c in ctxs])
+    _check(library().rte_adjoint_gradient_batch(carr, n, darr, ndet, meas, J, ga, gb), "rte_adjoint_gradient_batch")
+    return [J[k] for k in range(n)]
 
 
 def rte_set_pass_variant(ctx, variant: int):

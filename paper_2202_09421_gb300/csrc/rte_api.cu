@@ -68,8 +68,9 @@ struct rte_ctx {
   size_t n_timed = 0;
   // adjoint scratch
   DevBuf MU, RA, LA[3], seg, curves64, resid, partial, Jdev, rho, grad_a, grad_b, Wd, Wn, lohi;
-  // batched forward: device copy of the problem table
-  DevBuf batch_tab;
+  // batched forward: device copy of the problem table; batched adjoint: its
+  // adjoint-march table and its gradient / state-save job tables
+  DevBuf batch_tab, batch_tab_adj, batch_jobs;
   // CUDA-graph form of the forward march (RTE_FLAG_CUDA_GRAPH): the graph is
   // captured and replayed on a private stream ordered after the context's
   // stream by events, and re-captured when its key (sizes and every buffer
@@ -701,6 +702,8 @@ rte_status rte_destroy(rte_ctx* c) {
                    &c->bct_src, &c->bct_f, &c->fxp, &c->fyp, &c->FxT, &c->FyT};
   for (DevBuf* b : all) release(*b);
   release(c->batch_tab);
+  release(c->batch_tab_adj);
+  release(c->batch_jobs);
   release(c->err);
   release(c->bal);
   release(c->bal_partial);
@@ -1240,6 +1243,185 @@ rte_status rte_discrete_adjoint_gradient(rte_ctx* c, const rte_detector* dets, i
                                          const float* measured, double* J_out, float* dJ_dmua,
                                          float* dJ_dmus) {
   return adjoint_impl(c, dets, n_det, measured, J_out, dJ_dmua, dJ_dmus, true);
+}
+
+rte_status rte_adjoint_gradient_batch(rte_ctx* const* ctxs, int n_ctx, const rte_detector* const* dets,
+                                      const int* n_det, const float* const* measured, double* J_out,
+                                      float* const* dJ_dmua, float* const* dJ_dmus) {
+  if (!ctxs || n_ctx <= 0 || n_ctx > kMaxBatch || !dets || !n_det || !measured || !J_out) return RTE_ERR_INVALID_ARG;
+  rte_ctx* c0 = ctxs[0];
+  if (!c0) return RTE_ERR_INVALID_ARG;
+  for (int i = 0; i < n_ctx; ++i) {
+    rte_ctx* c = ctxs[i];
+    if (!c || !dets[i] || n_det[i] <= 0 || !measured[i]) return RTE_ERR_INVALID_ARG;
+    if (c->M != c0->M || c->tc_mode != c0->tc_mode || c->par.flags != c0->par.flags || c->stream != c0->stream)
+      return RTE_ERR_INVALID_ARG;
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == c) return RTE_ERR_INVALID_ARG;
+    if (c->n_steps <= 0 || c->par.ckpt_interval <= 0) return RTE_ERR_STATE;
+    if (c->n_steps != c0->n_steps || c->par.ckpt_interval != c0->par.ckpt_interval) return RTE_ERR_INVALID_ARG;
+    for (int d = 0; d < n_det[i]; ++d)
+      if (!(dets[i][d].sigma_d > 0)) return RTE_ERR_INVALID_ARG;
+  }
+  if (c0->tc_mode == 0) {
+    // plain FP32 form: one medium after another
+    for (int i = 0; i < n_ctx; ++i)
+      RTE_TRY(adjoint_impl(ctxs[i], dets[i], n_det[i], measured[i], &J_out[i], dJ_dmua ? dJ_dmua[i] : nullptr,
+                           dJ_dmus ? dJ_dmus[i] : nullptr, false));
+    return RTE_OK;
+  }
+  const int N = c0->n_steps, I = c0->par.ckpt_interval;
+  const cudaStream_t st = c0->stream;
+  // Per medium: detector curves, objective, adjoint boundary data rho of eq.
+  // (AdjointProblem), zeroed gradients and adjoint state (as adjoint_impl).
+  int max_ncell = 0;
+  std::vector<rte_kern::GradJob> gjobs(n_ctx);
+  std::vector<rte_kern::SaveJob> sjobs(n_ctx);
+  std::vector<std::vector<float>> keep_f;               // host tables alive until the copies are done
+  std::vector<std::vector<int>> keep_i;
+  for (int i = 0; i < n_ctx; ++i) {
+    rte_ctx* c = ctxs[i];
+    const int G = c->G;
+    const size_t gfloats = static_cast<size_t>(G) * c->plane, gbytes = gfloats * sizeof(float);
+    const size_t ncurve = static_cast<size_t>(G) * n_det[i] * N;
+    const size_t ncell = static_cast<size_t>(c->nx) * c->ny;
+    std::vector<float> Wd, Wn;
+    std::vector<int> lohi, lohi_n;
+    detector_weights(c, dets[i], n_det[i], true, Wd, lohi);
+    detector_weights(c, dets[i], n_det[i], false, Wn, lohi_n);
+    RTE_TRY(upload(c->Wd, Wd, st));
+    RTE_TRY(upload(c->Wn, Wn, st));
+    RTE_TRY(upload(c->lohi, lohi, st));
+    keep_f.push_back(std::move(Wd));
+    keep_f.push_back(std::move(Wn));
+    keep_i.push_back(std::move(lohi));
+    RTE_TRY(ensure(c->curves64, ncurve * sizeof(double)));
+    RTE_TRY(ensure(c->resid, ncurve * sizeof(float)));
+    RTE_TRY(ensure(c->partial, 256 * sizeof(double)));
+    RTE_TRY(ensure(c->Jdev, sizeof(double)));
+    RTE_TRY(ensure(c->rho, static_cast<size_t>(G) * N * c->ring_len * sizeof(float)));
+    RTE_TRY(ensure(c->grad_a, ncell * sizeof(double)));
+    RTE_TRY(ensure(c->grad_b, ncell * sizeof(double)));
+    RTE_TRY(ensure(c->MU, gbytes));
+    RTE_TRY(ensure(c->RA, gbytes));
+    for (int q = 0; q < 3; ++q) RTE_TRY(ensure(c->LA[q], gbytes));
+    RTE_TRY(ensure(c->seg, static_cast<size_t>(I) * gbytes));   // one segment of recomputed states
+    const int* lo = static_cast<const int*>(c->lohi.p);
+    RTE_TRY(cuda_status(rte_kern::launch_readout(F(c->ring), c->ring_len, N, G, F(c->Wd), lo, lo + n_det[i],
+                                                 n_det[i], nullptr, D(c->curves64), st, &c0->launches)));
+    RTE_TRY(cuda_status(rte_kern::launch_objective(D(c->curves64), measured[i], ncurve, c->par.dt, F(c->resid),
+                                                   D(c->partial), D(c->Jdev), st, &c0->launches)));
+    RTE_TRY(cuda_status(rte_kern::launch_rho(F(c->resid), F(c->Wn), n_det[i], c->ring_len, N, G, 1.0f, F(c->rho),
+                                             st, &c0->launches)));
+    RTE_TRY(cuda_status(cudaMemsetAsync(c->grad_a.p, 0, ncell * sizeof(double), st)));
+    RTE_TRY(cuda_status(cudaMemsetAsync(c->grad_b.p, 0, ncell * sizeof(double), st)));
+    RTE_TRY(cuda_status(cudaMemsetAsync(c->MU.p, 0, gbytes, st)));
+    for (int q = 0; q < 3; ++q) RTE_TRY(cuda_status(cudaMemsetAsync(c->LA[q].p, 0, gbytes, st)));
+    rte_kern::GradJob& gj = gjobs[i];
+    gj.MU = F(c->MU);
+    gj.seg = F(c->seg);
+    gj.slot_floats = gfloats;
+    gj.PT = F(c->PT);
+    gj.area = F(c->area);
+    gj.ncell = static_cast<long long>(ncell);
+    gj.M = c->M;
+    gj.G = G;
+    gj.plane = c->plane;
+    gj.scale = (2.0 * kPi / c->M) * c->par.dt;
+    gj.grad_a = (dJ_dmua && dJ_dmua[i]) ? D(c->grad_a) : nullptr;
+    gj.grad_b = (dJ_dmus && dJ_dmus[i]) ? D(c->grad_b) : nullptr;
+    sjobs[i] = rte_kern::SaveJob{F(c->U), F(c->seg), gfloats};
+    max_ncell = std::max(max_ncell, static_cast<int>(ncell));
+  }
+  // Tables of the recompute (forward boundary data, no exitance ring) and of
+  // the adjoint march (residual injection), media with the longest lines
+  // first, as in rte_forward_batch.
+  std::vector<int> order(n_ctx);
+  for (int i = 0; i < n_ctx; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return std::max(ctxs[x]->nx, ctxs[x]->ny) > std::max(ctxs[y]->nx, ctxs[y]->ny);
+  });
+  std::vector<rte_kern::BatchProblem> tf(n_ctx), ta(n_ctx);
+  for (int r = 0; r < n_ctx; ++r) {
+    rte_ctx* c = ctxs[order[r]];
+    rte_kern::BatchProblem& P = tf[r];
+    P.a = step_args(c, c->G);
+    P.b = boundary_args(c);
+    P.b.S = F(c->S); P.b.A = F(c->A); P.b.T = F(c->T); P.b.kmax = c->kmax; P.b.T_len = N;
+    P.U = F(c->U);
+    P.R = F(c->R);
+    for (int q = 0; q < 3; ++q) P.L[q] = F(c->L[q]);
+    rte_kern::BatchProblem& Q = ta[r];
+    Q.a = step_args(c, c->G);
+    Q.b = boundary_args(c);
+    Q.b.rho = F(c->rho); Q.b.rho_len = N;
+    Q.U = F(c->MU);
+    Q.R = F(c->RA);
+    for (int q = 0; q < 3; ++q) Q.L[q] = F(c->LA[q]);
+  }
+  int cx = 0, cy = 0;
+  rte_kern::tc_batch_layout(tf.data(), n_ctx, &cx, &cy);
+  rte_kern::tc_batch_layout(ta.data(), n_ctx, &cx, &cy);
+  RTE_TRY(upload(c0->batch_tab, tf, st));
+  RTE_TRY(upload(c0->batch_tab_adj, ta, st));
+  const size_t jg = gjobs.size() * sizeof(rte_kern::GradJob), js = sjobs.size() * sizeof(rte_kern::SaveJob);
+  RTE_TRY(ensure(c0->batch_jobs, jg + js));
+  RTE_TRY(cuda_status(cudaMemcpyAsync(c0->batch_jobs.p, gjobs.data(), jg, cudaMemcpyHostToDevice, st)));
+  RTE_TRY(cuda_status(cudaMemcpyAsync(static_cast<char*>(c0->batch_jobs.p) + jg, sjobs.data(), js,
+                                      cudaMemcpyHostToDevice, st)));
+  RTE_TRY(cuda_status(cudaStreamSynchronize(st)));      // the host tables can go
+  const auto* tf_dev = static_cast<const rte_kern::BatchProblem*>(c0->batch_tab.p);
+  const auto* ta_dev = static_cast<const rte_kern::BatchProblem*>(c0->batch_tab_adj.p);
+  const auto* gj_dev = static_cast<const rte_kern::GradJob*>(c0->batch_jobs.p);
+  const auto* sj_dev = reinterpret_cast<const rte_kern::SaveJob*>(static_cast<const char*>(c0->batch_jobs.p) + jg);
+
+  // Segments in reverse: recompute the segment's forward levels of every
+  // medium from its checkpoint (one x- and one y-pass launch per step over
+  // all media, then one launch saving every medium's state), then the
+  // adjoint steps of eq. (AdjointProblem) and their gradient terms (eq.
+  // FDwin22) for levels s_end - 1 .. s0, again one launch of each kind per
+  // level for all media.
+  const int last = N - 2;
+  int hl_adj = 0;
+  for (int seg = c0->n_ckpt - 1; seg >= 0; --seg) {
+    if (seg * I > last) continue;
+    const int s0 = seg * I, s_end = std::min(s0 + I, last + 1);
+    for (int i = 0; i < n_ctx; ++i) {
+      rte_ctx* c = ctxs[i];
+      const size_t gbytes = static_cast<size_t>(c->G) * c->plane * sizeof(float);
+      const char* base = static_cast<const char*>(c->ckpt.p) + static_cast<size_t>(seg) * 4 * gbytes;
+      RTE_TRY(cuda_status(cudaMemcpyAsync(c->U.p, base, gbytes, cudaMemcpyDeviceToDevice, st)));
+      for (int q = 0; q < 3; ++q)
+        RTE_TRY(cuda_status(cudaMemcpyAsync(c->L[q].p, base + (q + 1) * gbytes, gbytes, cudaMemcpyDeviceToDevice, st)));
+    }
+    int hl = 0;
+    for (int s = s0; s < s_end; ++s) {
+      RTE_TRY(cuda_status(rte_kern::launch_step_tc_batched(tf.data(), tf_dev, n_ctx, s, hl, st, &c0->launches)));
+      RTE_TRY(cuda_status(rte_kern::launch_save_batch(sj_dev, n_ctx, s - s0, st, &c0->launches)));
+      hl = (hl + 2) % 3;
+    }
+    for (int lvl = s_end - 1; lvl >= s0; --lvl) {
+      RTE_TRY(cuda_status(rte_kern::launch_step_tc_batched(ta.data(), ta_dev, n_ctx, lvl, hl_adj, st, &c0->launches)));
+      hl_adj = (hl_adj + 2) % 3;
+      RTE_TRY(cuda_status(rte_kern::launch_grad_batch(gj_dev, n_ctx, max_ncell, lvl - s0, 1, st, &c0->launches)));
+    }
+  }
+  for (int i = 0; i < n_ctx; ++i) {
+    rte_ctx* c = ctxs[i];
+    const size_t ncell = static_cast<size_t>(c->nx) * c->ny;
+    if (dJ_dmua && dJ_dmua[i])
+      RTE_TRY(cuda_status(rte_kern::launch_to_float(D(c->grad_a), dJ_dmua[i], ncell, st, &c0->launches)));
+    if (dJ_dmus && dJ_dmus[i])
+      RTE_TRY(cuda_status(rte_kern::launch_to_float(D(c->grad_b), dJ_dmus[i], ncell, st, &c0->launches)));
+    RTE_TRY(cuda_status(cudaMemcpyAsync(&J_out[i], c->Jdev.p, sizeof(double), cudaMemcpyDeviceToHost, st)));
+  }
+  RTE_TRY(cuda_status(cudaStreamSynchronize(st)));
+  rte_status res = RTE_OK;
+  for (int i = 0; i < n_ctx; ++i) {
+    const rte_status si = tc_check(ctxs[i]);
+    if (res == RTE_OK) res = si;
+  }
+  return res;
 }
 
 }  // extern "C"

@@ -417,14 +417,15 @@ __global__ void rho_kernel(const float* __restrict__ resid, const float* __restr
   rho[idx] = scale * acc;
 }
 
-__global__ void grad_kernel(const float* __restrict__ MU, const float* __restrict__ Useg,
-                            const float* __restrict__ PT, const float* __restrict__ area, int ncell,
-                            int M, int G, size_t plane, size_t useg_gs, double scale, int flip,
-                            double* __restrict__ grad_a, double* __restrict__ grad_b) {
+// One warp per grid cell: the gradient terms of eq. (FDwin22) summed over the
+// groups and the ordinates (see launch_grad).
+__device__ __forceinline__ void grad_cell(const float* __restrict__ MU, const float* __restrict__ Useg,
+                                          const float* __restrict__ PT, const float* __restrict__ area,
+                                          long long cell, int M, int G, size_t plane, size_t useg_gs,
+                                          double scale, int flip, double* __restrict__ grad_a,
+                                          double* __restrict__ grad_b) {
   __shared__ float ubuf[8][64];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  const long long cell = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  if (cell >= ncell) return;   // whole warp exits together
   float sa = 0.f, sb = 0.f;
   for (int g = 0; g < G; ++g) {
     const float* u = Useg + static_cast<size_t>(g) * useg_gs + static_cast<size_t>(cell) * M;
@@ -447,6 +448,36 @@ __global__ void grad_kernel(const float* __restrict__ MU, const float* __restric
     if (grad_a) grad_a[cell] -= k * static_cast<double>(sa);
     if (grad_b) grad_b[cell] -= k * static_cast<double>(sb);
   }
+}
+
+__global__ void grad_kernel(const float* __restrict__ MU, const float* __restrict__ Useg,
+                            const float* __restrict__ PT, const float* __restrict__ area, int ncell,
+                            int M, int G, size_t plane, size_t useg_gs, double scale, int flip,
+                            double* __restrict__ grad_a, double* __restrict__ grad_b) {
+  const long long cell = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (cell >= ncell) return;   // whole warp exits together
+  grad_cell(MU, Useg, PT, area, cell, M, G, plane, useg_gs, scale, flip, grad_a, grad_b);
+}
+
+// Batched forms for media that march in lockstep: blockIdx.y picks the
+// medium; its forward state of the level sits in slot `slot` of its segment
+// buffer.
+__global__ void grad_batch_kernel(const GradJob* __restrict__ jobs, int slot, int flip) {
+  const GradJob& j = jobs[blockIdx.y];
+  const long long cell = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (cell >= j.ncell) return;
+  grad_cell(j.MU, j.seg + static_cast<size_t>(slot) * j.slot_floats, j.PT, j.area, cell, j.M, j.G, j.plane,
+            j.plane, j.scale, flip, j.grad_a, j.grad_b);
+}
+
+__global__ void save_batch_kernel(const SaveJob* __restrict__ jobs, int slot) {
+  const SaveJob& j = jobs[blockIdx.y];
+  const size_t n4 = j.n_floats / 4;
+  const float4* src = reinterpret_cast<const float4*>(j.src);
+  float4* dst = reinterpret_cast<float4*>(j.seg + static_cast<size_t>(slot) * j.n_floats);
+  for (size_t k = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < n4;
+       k += static_cast<size_t>(gridDim.x) * blockDim.x)
+    dst[k] = src[k];
 }
 
 __global__ void to_float_kernel(const double* in, float* out, size_t n) {
@@ -654,6 +685,21 @@ cudaError_t launch_rho(const float* resid, const float* Wn, int n_det, int ring_
   if (total == 0) return cudaSuccess;
   rho_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(resid, Wn, n_det, ring_len,
                                                                          n_steps, G, scale, rho);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_batch(const GradJob* jobs_dev, int n_jobs, int max_ncell, int slot, int flip,
+                              cudaStream_t s, long long* launches) {
+  dim3 grid((max_ncell * 32 + 255) / 256, n_jobs);
+  grad_batch_kernel<<<grid, 256, 0, s>>>(jobs_dev, slot, flip);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_save_batch(const SaveJob* jobs_dev, int n_jobs, int slot, cudaStream_t s, long long* launches) {
+  dim3 grid(148, n_jobs);
+  save_batch_kernel<<<grid, 256, 0, s>>>(jobs_dev, slot);
   if (launches) *launches += 1;
   return cudaGetLastError();
 }

@@ -193,6 +193,34 @@ cudaError_t launch_balance(const float* U, size_t plane, int nx, int ny, int M, 
                            unsigned* ticket, double* out, int step, int n_steps, cudaStream_t s,
                            long long* launches);
 
+// Batched gradient and state save for media that march in lockstep (one
+// launch per step over all media).  Per medium: its adjoint field, the
+// segment buffer of its recomputed forward states (slot k at
+// seg + k * slot_floats), and what launch_grad takes; the gradient weight of
+// a cell is scale * area[cell] (dtheta dt times the trapezoid node area of
+// the continuous adjoint, eq. FDwin22).
+struct GradJob {
+  const float* MU;
+  const float* seg;
+  size_t slot_floats;
+  const float* PT;
+  const float* area;
+  long long ncell;
+  int M, G;
+  size_t plane;
+  double scale;
+  double* grad_a;
+  double* grad_b;
+};
+struct SaveJob {
+  const float* src;
+  float* seg;
+  size_t n_floats;                  // a multiple of 4
+};
+cudaError_t launch_grad_batch(const GradJob* jobs_dev, int n_jobs, int max_ncell, int slot, int flip,
+                              cudaStream_t s, long long* launches);
+cudaError_t launch_save_batch(const SaveJob* jobs_dev, int n_jobs, int slot, cudaStream_t s, long long* launches);
+
 cudaError_t launch_to_float(const double* in, float* out, size_t n, cudaStream_t s,
                             long long* launches);
 

@@ -115,6 +115,16 @@ def forward_batch(solvers, groups_per_solver, n_steps: int):
         s.n_groups, s.n_steps = len(groups), n_steps
 
 
+def adjoint_gradient_batch(solvers, detectors_per_solver, measured_per_solver):
+    """The continuous adjoint of every solver after a march of the same steps
+    (rte_adjoint_gradient_batch): a list of (J, dJ/dmua, dJ/dmus) per solver."""
+    gas = [torch.empty((s.grid.ny, s.grid.nx), device=s.device, dtype=torch.float32) for s in solvers]
+    gbs = [torch.empty_like(g) for g in gas]
+    Js = B.rte_adjoint_gradient_batch([s.ctx for s in solvers], detectors_per_solver,
+                                      [m.contiguous() for m in measured_per_solver], gas, gbs)
+    return list(zip(Js, gas, gbs))
+
+
 class RTEObjective(torch.autograd.Function):
     """J(mua, mus) = sum over groups of eq. (FObj) for the given beams and
     detectors.  forward: rte_forward + rte_objective; backward: the adjoint

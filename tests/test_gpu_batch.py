@@ -162,3 +162,49 @@ def test_batch_rejects_mixed_settings():
         forward_batch([sa, sa], [wa.groups, wa.groups], 10)
     assert err.value.status == 1
     sa.close(); sb.close()
+
+
+@pytest.mark.parametrize("precision", [TF32X3, FP32])
+def test_batched_adjoint_equals_each_medium_alone(precision):
+    """rte_adjoint_gradient_batch after a batched march: every medium's J and
+    gradients equal its own rte_adjoint_gradient (same kernel bodies and
+    operation order, checkpoints of the same march), bit for bit; one
+    medium's against the FP64 oracle's continuous adjoint."""
+    from oracle.rte import Solver
+    from paper_2202_09421_gb300.solver import adjoint_gradient_batch, forward_batch
+    wls = _media(16, [(40, 36, 2), (48, 40, 1), (33, 35, 1)], n_steps=70)
+    ss = [_solver(w, precision, ckpt=20) for w in wls]
+    forward_batch(ss, [w.groups for w in wls], wls[0].n_steps)
+    meas = [0.8 * s.readout(w.detectors) for s, w in zip(ss, wls)]
+    got = adjoint_gradient_batch(ss, [w.detectors for w in wls], meas)
+    for s, w, m, (J, ga, gb) in zip(ss, wls, meas, got):
+        J1, ga1, gb1 = s.adjoint_gradient(w.detectors, m)
+        assert J == J1
+        assert torch.equal(ga, ga1) and torch.equal(gb, gb1)
+        assert float(ga.abs().max()) > 0
+    w, (J, ga, gb) = wls[1], got[1]
+    S = Solver(w)
+    mref = meas[1].double().cpu().numpy()
+    Jo, gao, gbo = 0.0, 0.0, 0.0
+    for k, g in enumerate(w.groups):
+        j, a_, b_, _ = S.adjoint_gradient(g, w.n_steps, w.detectors, mref[k])
+        Jo, gao, gbo = Jo + j, gao + a_, gbo + b_
+    assert abs(J - Jo) < 1e-5 * abs(Jo)
+    assert rel_l2(ga.cpu(), gao) < 1e-4 and rel_l2(gb.cpu(), gbo) < 1e-4
+    for s in ss:
+        s.close()
+
+
+def test_batched_adjoint_rejects_mixed_step_counts():
+    from paper_2202_09421_gb300 import binding as B
+    from paper_2202_09421_gb300.solver import adjoint_gradient_batch
+    wls = _media(16, [(40, 36, 1), (33, 35, 1)], n_steps=40)
+    ss = [_solver(w, TF32X3, ckpt=10) for w in wls]
+    ss[0].forward(wls[0].groups, 40)
+    ss[1].forward(wls[1].groups, 30)
+    meas = [torch.zeros((len(w.groups), len(w.detectors), n), device="cuda:0") for w, n in zip(wls, (40, 30))]
+    with pytest.raises(B.RTEError) as e:
+        adjoint_gradient_batch(ss, [w.detectors for w in wls], meas)
+    assert e.value.status == 1
+    for s in ss:
+        s.close()
