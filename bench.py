@@ -64,6 +64,9 @@ NCU_TRAFFIC = {
     # profiles/tc_stream_passes_tomo256_ncu.md
     ("tc_xpass_stream", "8a761a4512d9f193"): 135.925760e6 + 90.829568e6,
     ("tc_pass_kernel<y>", "afb6b0b13f1a4d3e"): 689.004032e6 + 188.723456e6,
+    # tile-local fused step (csrc/rte_fused.cu), 16 x 16 parts:
+    # profiles/fused_step_tomo256_ncu_full.md
+    ("fused_step_kernel", "09d63ccdc8189d08"): 538.545920e6 + 231.291136e6,
 }
 
 
