@@ -62,8 +62,8 @@ NCU_TRAFFIC = {
     # TMA-fed x-pass (csrc/rte_tc_stream.cu + rte_tc_common.cuh) and the
     # one-tile y-pass (csrc/rte_tc.cu + rte_tc_common.cuh), schedule 4:
     # profiles/tc_stream_passes_tomo256_ncu.md
-    ("tc_xpass_stream", "8a761a4512d9f193"): 135.925760e6 + 90.829568e6,
-    ("tc_pass_kernel<y>", "afb6b0b13f1a4d3e"): 689.004032e6 + 188.723456e6,
+    ("tc_pass_stream<x>", "21974cd08a6aab48"): 139.259392e6 + 90.189568e6,
+    ("tc_pass_kernel<y>", "f449e53167e517f9"): 689.023744e6 + 188.668928e6,
     # tile-local fused step (csrc/rte_fused.cu), 16 x 16 parts:
     # profiles/fused_step_tomo256_ncu_full.md
     ("fused_step_kernel", "09d63ccdc8189d08"): 538.545920e6 + 231.291136e6,
@@ -76,7 +76,7 @@ def kernel_source_hash(name="tc_pass_ws"):
         srcs = ["rte_tc_ws.cu", "rte_tc_common.cuh"]
     elif name.startswith("tc_ypass_pipe"):
         srcs = ["rte_tc_pipe.cu", "rte_tc_common.cuh"]
-    elif name.startswith("tc_xpass_stream"):
+    elif name.startswith("tc_pass_stream"):
         srcs = ["rte_tc_stream.cu", "rte_tc_common.cuh"]
     elif name.startswith("tc_pass"):
         srcs = ["rte_tc.cu", "rte_tc_common.cuh"]
@@ -102,7 +102,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=40)
     ap.add_argument("--schedule", default="auto",
-                    choices=["auto", "one-tile", "persistent", "pipelined", "stream"],
+                    choices=["auto", "one-tile", "persistent", "pipelined", "stream", "stream-xy"],
                     help="tensor-core pass schedule: autotuned, one tile per CTA (the default "
                          "configuration), persistent warp-specialised, one-tile x-pass with the "
                          "pipelined persistent y-pass, or the TMA-fed persistent x-pass")
@@ -312,7 +312,7 @@ def run_ours(args):
         elif schedule == "auto":
             tuned = solver.autotune(wl.groups, 40)
         else:
-            variant = {"persistent": 0, "one-tile": 1, "pipelined": 2, "stream": 4}[schedule]
+            variant = {"persistent": 0, "one-tile": 1, "pipelined": 2, "stream": 4, "stream-xy": 5}[schedule]
             B.rte_set_pass_variant(solver.ctx, variant)
             tuned = (variant, {})
 
@@ -365,12 +365,14 @@ def run_ours(args):
     # against HBM.
     ncell_m = g.nx * g.ny * g.M * len(wl.groups)
     step_gbs = 24.0 * updates / (ms_step / 1e3) / 1e9
-    # the configuration timed: schedule = choice % 5 (0 persistent
+    # the configuration timed: schedule = choice % 6 (0 persistent
     # warp-specialised, 1 one tile per CTA, 2 pipelined y-pass, 4 TMA-fed
-    # persistent x-pass), choice >= 5 tensor-core scattering
-    sched = tuned[0] % 5
+    # persistent x-pass, 5 TMA-fed persistent x- and y-passes), choice >= 6
+    # tensor-core scattering
+    sched = tuned[0] % 6
     names = {0: ["tc_pass_ws<x>", "tc_pass_ws<y>"], 1: ["tc_pass_kernel<x>", "tc_pass_kernel<y>"],
-             2: ["tc_pass_kernel<x>", "tc_ypass_pipe<y>"], 4: ["tc_xpass_stream", "tc_pass_kernel<y>"]}[sched]
+             2: ["tc_pass_kernel<x>", "tc_ypass_pipe<y>"], 4: ["tc_pass_stream<x>", "tc_pass_kernel<y>"],
+             5: ["tc_pass_stream<x>", "tc_pass_stream<y>"]}[sched]
     per_launch = [pass_ms[k] / max(1, pass_cnt[k]) for k in range(2)]
     x_gbs = 8.0 * ncell_m / (per_launch[0] / 1e3) / 1e9
     x_tflops = 3 * 2 * (g.nx + g.M) * ncell_m / (per_launch[0] / 1e3) / 1e12
@@ -436,7 +438,7 @@ def run_ours(args):
     # photon count, and the cost of recording it.
     sb = FCDOMSolver(g, wl.optics, a, b, wl.c, wl.dt, precision=B.RTE_PREC_TF32X3,
                      flags=B.RTE_FLAG_PHOTON_BALANCE)
-    B.rte_set_pass_variant(sb.ctx, tuned[0] % 5)
+    B.rte_set_pass_variant(sb.ctx, tuned[0] % 6)
     sb.forward(wl.groups, wl.n_steps)
     ms_bal = max_over_ranks(_timed(lambda: sb.forward(wl.groups, wl.n_steps), stream, flush, barrier))
     bal = sb.photon_balance().cpu().numpy()
@@ -537,9 +539,9 @@ def run_ours(args):
             "config": {"workload": WORKLOAD_DESC,
                        "form": "tcgen05 tensor cores, split 3xTF32 operands (FP32-level accuracy)",
                        "autotune": {"choice": tuned[0], "trial_ms_per_40_steps": tuned[1],
-                                    "choices": "choice % 5: 0 persistent warp-specialised, 1 one tile per "
-                                               "CTA, 2 pipelined y-pass, 4 TMA-fed persistent x-pass; "
-                                               "choice >= 5: tensor-core scattering"},
+                                    "choices": "choice % 6: 0 persistent warp-specialised, 1 one tile per "
+                                               "CTA, 2 pipelined y-pass, 4 TMA-fed persistent x-pass, 5 TMA-fed "
+                                               "persistent x- and y-passes; choice >= 6: tensor-core scattering"},
                        "updates_per_step": updates * world, "l2": "flushed between timed steps "
                        "(256 MB write) and state > L2", "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -359,7 +359,18 @@ long long rte_graph_captures(const rte_ctx* ctx);
  *      precision; where supported (fc_parts_x, fc_parts_y >= 2 with owned
  *      ranges of at most 16 points, M in {16, 32}) by rte_forward and
  *      rte_adjoint_gradient (rte_discrete_adjoint_gradient and the batched
- *      and allocation-free forwards run the one-tile-per-CTA passes).
+ *      and allocation-free forwards run the one-tile-per-CTA passes);
+ *   4  persistent TMA-fed x-pass (one CTA per SM; the raw slab arrives by
+ *      tensor copies and converter warps split it into the tensor-core
+ *      operands) and the one-tile-per-CTA y-pass, where supported
+ *      (RTE_PREC_TF32X3 and RTE_PREC_TF32, nx <= 256, M in {16, 32}, no
+ *      RTE_FLAG_TC_SCATTER);
+ *   5  persistent TMA-fed x- and y-passes, where supported (as 4, and
+ *      ny <= 256 for the y-pass).
+ * Schedules 4 and 5 give the one-tile-per-CTA passes' results bit for bit.
+ * rte_discrete_adjoint_gradient, rte_forward_batch and
+ * rte_adjoint_gradient_batch run the one-tile-per-CTA passes under every
+ * schedule.
  * Unsupported sizes run the one-tile-per-CTA passes (the plain FP32 passes
  * in RTE_PREC_FP32).  Errors: INVALID_ARG. */
 rte_status rte_set_pass_variant(rte_ctx* ctx, int variant);
@@ -388,11 +399,12 @@ rte_status rte_inject_fault(rte_ctx* ctx, int kind);
  * the context's precision admits, with CUDA events around one forward of
  * n_trial_steps (>= 4) of the given groups after an untimed one, and keeps
  * the fastest in the context.  A configuration is choice = schedule +
- * 3 * (1 if the x-pass scattering is the tensor-core contraction), with the
- * schedule of rte_set_pass_variant (0, 1, 2) and RTE_FLAG_TC_SCATTER.
+ * 6 * (1 if the x-pass scattering is the tensor-core contraction), with the
+ * schedule of rte_set_pass_variant (0, 1, 2, 4, 5; never 3, which is chosen
+ * with the decomposition) and RTE_FLAG_TC_SCATTER.
  * Configurations a size does not support are skipped; all of them meet the
  * precision's parity bound.  *choice_out receives the chosen configuration,
- * ms_out (host, 6 entries, may be NULL) the time of each configuration tried
+ * ms_out (host, 12 entries, may be NULL) the time of each configuration tried
  * (entries of the others are untouched).  The trial forwards replace the
  * context's last-forward results.  In RTE_PREC_FP32 there is one
  * configuration and nothing is run.  Errors: INVALID_ARG, the errors of

@@ -245,10 +245,10 @@ def rte_autotune(ctx, groups, n_trial_steps: int):
     for k, bl in enumerate(groups):
         garr[k] = RteSourceGroup(ctypes.cast(beam_arrays[k], POINTER(RteBeam)), len(bl))
     choice = c_int()
-    ms = (ctypes.c_float * 10)(*([-1.0] * 10))
+    ms = (ctypes.c_float * 12)(*([-1.0] * 12))
     _check(library().rte_autotune(ctx, garr, len(groups), int(n_trial_steps), ctypes.byref(choice), ms),
            "rte_autotune")
-    return choice.value, {k: ms[k] for k in range(10) if ms[k] >= 0.0}
+    return choice.value, {k: ms[k] for k in range(12) if ms[k] >= 0.0}
 
 
 def rte_graph_captures(ctx) -> int:

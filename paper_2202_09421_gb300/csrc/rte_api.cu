@@ -554,7 +554,7 @@ const char* rte_last_cuda_error(void) { return cudaGetErrorName(g_last_cuda_erro
 long long rte_graph_captures(const rte_ctx* ctx) { return ctx ? ctx->graph_captures : -1; }
 
 rte_status rte_set_pass_variant(rte_ctx* c, int variant) {
-  if (!c || variant < 0 || variant > 4) return RTE_ERR_INVALID_ARG;
+  if (!c || variant < 0 || variant > 5) return RTE_ERR_INVALID_ARG;
   c->x_variant = variant;
   return RTE_OK;
 }
@@ -569,14 +569,14 @@ rte_status rte_inject_fault(rte_ctx* c, int kind) {
 rte_status rte_autotune(rte_ctx* c, const rte_source_group* groups, int n_groups, int n_trial_steps,
                         int* choice_out, float* ms_out) {
   if (!c || !groups || n_groups <= 0 || n_trial_steps < 4 || !choice_out) return RTE_ERR_INVALID_ARG;
-  *choice_out = c->x_variant + ((c->par.flags & RTE_FLAG_TC_SCATTER) ? 5 : 0);
+  *choice_out = c->x_variant + ((c->par.flags & RTE_FLAG_TC_SCATTER) ? 6 : 0);
   if (c->tc_mode == 0) return RTE_OK;                     // one kernel family, nothing to choose
   rte_kern::StepArgs probe = step_args(c, n_groups);
-  // configurations: schedule (0, 1, 2, 4) + 5 x (tensor-core scattering)
+  // configurations: schedule (0, 1, 2, 4, 5) + 6 x (tensor-core scattering)
   std::vector<int> cands;
-  for (int choice = 0; choice < 10; ++choice) {
-    const int variant = choice % 5;
-    const bool scat = choice >= 5;
+  for (int choice = 0; choice < 12; ++choice) {
+    const int variant = choice % 6;
+    const bool scat = choice >= 6;
     if (variant == 3) continue;                           // the fused step: chosen with the decomposition
     if (scat && !rte_kern::tc_supported(c->nx, c->ny, c->M, c->tc_mode, RTE_FLAG_TC_SCATTER)) continue;
     probe.x_variant = variant;
@@ -585,6 +585,7 @@ rte_status rte_autotune(rte_ctx* c, const rte_source_group* groups, int n_groups
     if (variant == 0 && !rte_kern::tc_ws_supported(probe)) continue;
     if (variant == 2 && !rte_kern::tc_pipe_supported(probe)) continue;
     if (variant == 4 && !rte_kern::tc_stream_supported(probe)) continue;
+    if (variant == 5 && !rte_kern::tc_ystream_supported(probe)) continue;
     cands.push_back(choice);
   }
   const int keep_variant = c->x_variant, keep_flags = c->par.flags;
@@ -597,9 +598,9 @@ rte_status rte_autotune(rte_ctx* c, const rte_source_group* groups, int n_groups
   int best_choice = -1;
   for (size_t k = 0; k < cands.size() && st == RTE_OK; ++k) {
     const int choice = cands[k];
-    c->x_variant = choice % 5;
-    c->par.flags = (keep_flags & ~RTE_FLAG_TC_SCATTER) | (choice >= 5 ? RTE_FLAG_TC_SCATTER : 0);
-    if (choice >= 5) st = ensure_phase_image(c);
+    c->x_variant = choice % 6;
+    c->par.flags = (keep_flags & ~RTE_FLAG_TC_SCATTER) | (choice >= 6 ? RTE_FLAG_TC_SCATTER : 0);
+    if (choice >= 6) st = ensure_phase_image(c);
     // one untimed forward, then a timed one
     if (st == RTE_OK) st = rte_forward(c, groups, n_groups, n_trial_steps, nullptr, 0, nullptr);
     if (st == RTE_OK) st = cuda_status(cudaEventRecord(e0, c->stream));
@@ -622,8 +623,8 @@ rte_status rte_autotune(rte_ctx* c, const rte_source_group* groups, int n_groups
     c->par.flags = keep_flags;
     return st != RTE_OK ? st : RTE_ERR_STATE;
   }
-  c->x_variant = best_choice % 5;
-  c->par.flags = (keep_flags & ~RTE_FLAG_TC_SCATTER) | (best_choice >= 5 ? RTE_FLAG_TC_SCATTER : 0);
+  c->x_variant = best_choice % 6;
+  c->par.flags = (keep_flags & ~RTE_FLAG_TC_SCATTER) | (best_choice >= 6 ? RTE_FLAG_TC_SCATTER : 0);
   *choice_out = best_choice;
   return RTE_OK;
 }

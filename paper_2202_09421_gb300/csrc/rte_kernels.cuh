@@ -59,7 +59,8 @@ struct StepArgs {
   int tc_mode;
   int tc_scatter;                   // x-pass scattering as a tcgen05 contraction
   int x_variant;                    // 0 persistent warp-specialised passes, 1 one tile per CTA, 2 pipelined y-pass,
-                                    // 3 tile-local fused step, 4 TMA-fed persistent x-pass + one-tile y-pass
+                                    // 3 tile-local fused step, 4 TMA-fed persistent x-pass + one-tile y-pass,
+                                    // 5 TMA-fed persistent x- and y-passes
   const void* DxImg;
   const void* DyImg;
   const float* PImg;                // phase matrix as the scattering operand
@@ -137,11 +138,16 @@ bool tc_pipe_supported(const StepArgs& a);
 cudaError_t launch_ypass_pipe(const StepArgs& a, const BoundaryArgs& b, float* U, const float* R, const float* L1,
                               const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s);
 
-// Persistent TMA-fed x-pass (rte_tc_stream.cu): TF32 operand kinds, nx <=
-// 256, M in {16, 32}, without the tensor-core scattering flag; the raw slab
-// arrives by tensor copies and is split into operands by converter warps.
+// Persistent TMA-fed passes (rte_tc_stream.cu): TF32 operand kinds, lines
+// of at most 256 points, M in {16, 32} (the x-pass without the tensor-core
+// scattering flag); the raw slab arrives by tensor copies and is split into
+// operands by converter warps.  Neither has the transposed step.
 bool tc_stream_supported(const StepArgs& a);
-cudaError_t launch_xpass_stream(const StepArgs& a, const float* U, float* R, cudaStream_t s);
+bool tc_ystream_supported(const StepArgs& a);
+cudaError_t launch_xpass_stream(const StepArgs& a, const BoundaryArgs& b, const float* U, float* R,
+                                cudaStream_t s);
+cudaError_t launch_ypass_stream(const StepArgs& a, const BoundaryArgs& b, float* U, float* R, const float* L1,
+                                const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s);
 
 // Tile-local fused step (rte_fused.cu): one launch per step over the
 // subdomains of the decomposed operator (parts >= 2 on both axes, owned

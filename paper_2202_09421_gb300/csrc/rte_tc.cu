@@ -569,10 +569,10 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
           }
           float4 lk, un;
           lk.x = r4.x + ac.x; lk.y = r4.y + ac.y; lk.z = r4.z + ac.z; lk.w = r4.w + ac.w;
-          un.x = fmaf(a.cdt, kAB0 * lk.x + kAB1 * p4.x + kAB2 * q4.x + kAB3 * s4.x, u4.x);
-          un.y = fmaf(a.cdt, kAB0 * lk.y + kAB1 * p4.y + kAB2 * q4.y + kAB3 * s4.y, u4.y);
-          un.z = fmaf(a.cdt, kAB0 * lk.z + kAB1 * p4.z + kAB2 * q4.z + kAB3 * s4.z, u4.z);
-          un.w = fmaf(a.cdt, kAB0 * lk.w + kAB1 * p4.w + kAB2 * q4.w + kAB3 * s4.w, u4.w);
+          un.x = ab4_node(a.cdt, lk.x, p4.x, q4.x, s4.x, u4.x);
+          un.y = ab4_node(a.cdt, lk.y, p4.y, q4.y, s4.y, u4.y);
+          un.z = ab4_node(a.cdt, lk.z, p4.z, q4.z, s4.z, u4.z);
+          un.w = ab4_node(a.cdt, lk.w, p4.w, q4.w, s4.w, u4.w);
           *reinterpret_cast<float4*>(L3 + gidx) = lk;
           if (chunk_bnd) *reinterpret_cast<float4*>(un_s + t * kNC + c) = un;
           if (!bnd) st_hint(U + gidx, un, pol_keep);   // u^{k+1} is read by the next x-pass
@@ -848,17 +848,20 @@ cudaError_t launch_step_tc(const StepArgs& a, const BoundaryArgs& b, float* U, f
   // the transposed step exists in the one-tile-per-CTA passes only
   const bool ws = a.x_variant == 0 && tc_ws_supported(a) && !b.bct_src;
   const bool pipe = a.x_variant == 2 && tc_pipe_supported(a) && !b.bct_src;
-  // the TMA-fed x-pass (its scattering sum is the same as the one-tile
-  // x-pass's; the transposed step uses the one-tile passes throughout)
-  const bool stream = a.x_variant == 4 && tc_stream_supported(a) && !b.bct_src && !a.test_expire;
+  // the TMA-fed passes (the same arithmetic as the one-tile passes; the
+  // transposed step uses the one-tile passes throughout)
+  const bool tma = (a.x_variant == 4 || a.x_variant == 5) && !b.bct_src && !a.test_expire;
+  const bool stream = tma && tc_stream_supported(a);
+  const bool ystream = tma && a.x_variant == 5 && tc_ystream_supported(a);
   e = ws       ? launch_pass_ws(true, a, b, U, R, L1, L2, L3, step, ring_step, s)
-      : stream ? launch_xpass_stream(a, U, R, s)
+      : stream ? launch_xpass_stream(a, b, U, R, s)
                : launch_mode<true>(a, b, U, R, L1, L2, L3, step, ring_step, s);
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[1], s);
-  e = ws     ? launch_pass_ws(false, a, b, U, R, L1, L2, L3, step, ring_step, s)
-      : pipe ? launch_ypass_pipe(a, b, U, R, L1, L2, L3, step, ring_step, s)
-             : launch_mode<false>(a, b, U, R, L1, L2, L3, step, ring_step, s);
+  e = ws        ? launch_pass_ws(false, a, b, U, R, L1, L2, L3, step, ring_step, s)
+      : pipe    ? launch_ypass_pipe(a, b, U, R, L1, L2, L3, step, ring_step, s)
+      : ystream ? launch_ypass_stream(a, b, U, R, L1, L2, L3, step, ring_step, s)
+                : launch_mode<false>(a, b, U, R, L1, L2, L3, step, ring_step, s);
   if (ev) cudaEventRecord(ev[2], s);
   if (launches) *launches += 2;
   return e;

@@ -26,6 +26,13 @@ __device__ __forceinline__ unsigned long long global_ns() {
 constexpr float kAB0 = 55.0f / 24.0f, kAB1 = -59.0f / 24.0f, kAB2 = 37.0f / 24.0f,
                 kAB3 = -9.0f / 24.0f;
 
+// AB4 update of one node value (eq. RTEAB4): u + c dt (55 L^k - 59 L^{k-1}
+// + 37 L^{k-2} - 9 L^{k-3}) / 24 with a fixed FMA order, so that every
+// y-pass schedule rounds it the same way.
+__device__ __forceinline__ float ab4_node(float cdt, float lk, float l1, float l2, float l3, float u) {
+  return fmaf(cdt, fmaf(kAB3, l3, fmaf(kAB2, l2, fmaf(kAB1, l1, kAB0 * lk))), u);
+}
+
 // Operand kinds of the precision modes (rte.h): 1 3xTF32, 2 TF32, 3 bf16x3,
 // 4 BF16.  KC = K positions per 128-byte row, GV = values per 16-byte group.
 template <int PREC>
@@ -153,6 +160,9 @@ __device__ __forceinline__ void st_hint(float* ptr, float4 v, uint64_t pol) {
                "f"(v.z), "f"(v.w), "l"(pol)
                : "memory");
 }
+__device__ __forceinline__ void st_hint1(float* ptr, float v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(ptr), "f"(v), "l"(pol) : "memory");
+}
 __device__ __forceinline__ float ld_hint(const float* ptr, uint64_t pol) {
   float v;
   asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(ptr), "l"(pol));
@@ -189,20 +199,49 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
 //   acc[m] = acc[m] - (a + b) u_m + sum_d p_d (b u_{(m - d) mod M}),
 // the circulant form of b P~u with p_d = P~[d][0] (P~[m][q] = p_{(m - q) mod M},
 // symmetric circulant).  The weights are read from shared memory, one
-// broadcast per d for all M outputs, so each d is M independent FMAs.
-// Overwrites uu with b u.
-template <int MM>
+// broadcast per d for all M outputs.  The sum runs over d in order for every
+// m.  PAIRED issues it on pairs of outputs (m, m + 1) with paired FP32 FMAs;
+// each half is the scalar fmaf, so both forms give the same bits (for even d
+// the pair reads (b u_j, b u_{j+1}) at even j, for odd d at odd j, so b u is
+// kept in both pairings).  Overwrites uu with b u.
+template <int MM, bool PAIRED = false>
 __device__ __forceinline__ void xpass_node_rhs(float (&acc)[MM], float (&uu)[MM], const float* psm, float ab,
                                                float bb) {
 #pragma unroll
   for (int m = 0; m < MM; ++m) acc[m] = fmaf(-ab, uu[m], acc[m]);
 #pragma unroll
   for (int m = 0; m < MM; ++m) uu[m] *= bb;
+  if constexpr (!PAIRED) {
 #pragma unroll
-  for (int d = 0; d < MM; ++d) {
-    const float pd = psm[d];
+    for (int d = 0; d < MM; ++d) {
+      const float pd = psm[d];
 #pragma unroll
-    for (int m = 0; m < MM; ++m) acc[m] = fmaf(pd, uu[(m - d + MM) % MM], acc[m]);
+      for (int m = 0; m < MM; ++m) acc[m] = fmaf(pd, uu[(m - d + MM) % MM], acc[m]);
+    }
+  } else {
+    constexpr int H = MM / 2;
+    float2 ev[H], od[H], ac[H];          // ev[k] = (bu_2k, bu_2k+1), od[k] = (bu_2k+1, bu_2k+2 mod M)
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      ev[k] = make_float2(uu[2 * k], uu[2 * k + 1]);
+      od[k] = make_float2(uu[2 * k + 1], uu[(2 * k + 2) % MM]);
+      ac[k] = make_float2(acc[2 * k], acc[2 * k + 1]);
+    }
+#pragma unroll
+    for (int d = 0; d < MM; ++d) {
+      const float pd = psm[d];
+      const float2 p2 = make_float2(pd, pd);
+#pragma unroll
+      for (int k = 0; k < H; ++k) {
+        const int j = (2 * k - d + MM) % MM;
+        ac[k] = __ffma2_rn(p2, (d & 1) ? od[(j - 1) / 2] : ev[j / 2], ac[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      acc[2 * k] = ac[k].x;
+      acc[2 * k + 1] = ac[k].y;
+    }
   }
 }
 

@@ -323,10 +323,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
             const float4 ac = *reinterpret_cast<const float4*>(acc_s + t * kNC + c);
             float4 lk, un;
             lk.x = r4.x + ac.x; lk.y = r4.y + ac.y; lk.z = r4.z + ac.z; lk.w = r4.w + ac.w;
-            un.x = fmaf(a.cdt, kAB0 * lk.x + kAB1 * p4.x + kAB2 * q4.x + kAB3 * s4.x, u4.x);
-            un.y = fmaf(a.cdt, kAB0 * lk.y + kAB1 * p4.y + kAB2 * q4.y + kAB3 * s4.y, u4.y);
-            un.z = fmaf(a.cdt, kAB0 * lk.z + kAB1 * p4.z + kAB2 * q4.z + kAB3 * s4.z, u4.z);
-            un.w = fmaf(a.cdt, kAB0 * lk.w + kAB1 * p4.w + kAB2 * q4.w + kAB3 * s4.w, u4.w);
+            un.x = ab4_node(a.cdt, lk.x, p4.x, q4.x, s4.x, u4.x);
+            un.y = ab4_node(a.cdt, lk.y, p4.y, q4.y, s4.y, u4.y);
+            un.z = ab4_node(a.cdt, lk.z, p4.z, q4.z, s4.z, u4.z);
+            un.w = ab4_node(a.cdt, lk.w, p4.w, q4.w, s4.w, u4.w);
             const size_t gidx = goff + (static_cast<size_t>(j) * nx + t0) * M + c;
             *reinterpret_cast<float4*>(L3 + gidx) = lk;
             const bool bnd = i == 0 || i == nx - 1 || j == 0 || j == ny - 1;

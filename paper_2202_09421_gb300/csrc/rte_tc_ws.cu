@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
           const float lk = rr[t] + acc[t];
-          un[t] = fmaf(a.cdt, kAB0 * lk + kAB1 * p1[t] + kAB2 * p2[t] + kAB3 * p3[t], uo[t]);
+          un[t] = ab4_node(a.cdt, lk, p1[t], p2[t], p3[t], uo[t]);
           const int j = j0c + t;
           if (col_ok && j < ny) L3[goff + (static_cast<size_t>(j) * nx + i) * M + m] = lk;
         }

@@ -199,10 +199,11 @@ def test_autotune_keeps_a_valid_configuration(precision):
     choice, ms = s.autotune(wl.groups, 12)
     print(f"autotune prec {precision}: choice {choice}, times {ms}")
     assert choice in ms and ms[choice] == min(ms.values())
-    # choice = schedule + 5 * TC scattering (schedules 0, 1, 2, 4); the
-    # persistent warp-specialised and the TMA-fed schedules have no TC
-    # scattering, the BF16 kinds none at all and no TMA-fed x-pass
-    expected = {0, 1, 2, 4, 6, 7} if precision == TF32X3 else {0, 1, 2}
+    # choice = schedule + 6 * TC scattering (schedules 0, 1, 2, 4, 5); the
+    # persistent warp-specialised schedule and the TMA-fed x-pass have no TC
+    # scattering (schedule 5 with it keeps its TMA-fed y-pass), the BF16
+    # kinds none at all and no TMA-fed passes
+    expected = {0, 1, 2, 4, 5, 7, 8, 11} if precision == TF32X3 else {0, 1, 2}
     assert set(ms) == expected
     s.forward(wl.groups, wl.n_steps)
     curves = s.readout(wl.detectors).cpu().numpy()
@@ -237,43 +238,76 @@ def test_pipelined_ypass_matches_oracle(nx, ny, M, groups, precision):
 
 
 @pytest.mark.parametrize("nx,ny,M,groups", [(256, 256, 32, 3), (100, 70, 32, 2), (200, 131, 16, 1),
-                                            (45, 29, 16, 5), (256, 37, 16, 2)])
+                                            (45, 29, 16, 5), (256, 37, 16, 2), (37, 256, 32, 1)])
 @pytest.mark.parametrize("precision", [TF32X3, TF32])
-def test_tma_fed_xpass_matches_one_tile_bitwise(nx, ny, M, groups, precision):
-    """Schedule 4's x-pass (persistent, raw slab by tensor copies, converter
-    warps) issues the same splits, the same MMAs in the same order and the
-    same epilogue arithmetic as the one-tile x-pass, so the states after a
-    march are bit for bit the same; ragged sizes exercise the zero fill of
-    the tensor copies past the last row and position."""
+def test_tma_fed_passes_match_one_tile_bitwise(nx, ny, M, groups, precision):
+    """Schedules 4 (TMA-fed x-pass) and 5 (TMA-fed x- and y-passes: raw slab
+    by tensor copies, converter warps, persistent CTAs) issue the same
+    splits, the same MMAs in the same order and the same epilogue arithmetic
+    as the one-tile passes, so the states and the detector curves (from the
+    y-pass's exitance) after a march are bit for bit the same; ragged sizes
+    exercise the zero fill of the tensor copies past the last line and
+    position, and the partial last tile of columns."""
     from paper_2202_09421_gb300 import binding as B
     from paper_2202_09421_gb300.solver import FCDOMSolver
     wl = _stable_custom(nx, ny, M, groups, n_steps=30)
     dev = torch.device("cuda:0")
-    states = []
-    for variant in (1, 4):
+    states, curves = [], []
+    for variant in (1, 4, 5):
         s = FCDOMSolver(wl.grid, wl.optics, torch.tensor(wl.mua, dtype=torch.float32, device=dev),
                         torch.tensor(wl.mus, dtype=torch.float32, device=dev), wl.c, wl.dt, precision=precision)
         B.rte_set_pass_variant(s.ctx, variant)
         s.forward(wl.groups, wl.n_steps)
         states.append([s.state(g).cpu().numpy() for g in range(groups)])
+        curves.append(s.readout(wl.detectors).cpu().numpy())
         s.close()
-    for a_, b_ in zip(states[0], states[1]):
-        assert np.abs(a_).max() > 0
-        assert np.array_equal(a_, b_)
+    for other in (1, 2):
+        for a_, b_ in zip(states[0], states[other]):
+            assert np.abs(a_).max() > 0
+            assert np.array_equal(a_, b_)
+        assert np.abs(curves[0]).max() > 0
+        assert np.array_equal(curves[0], curves[other])
 
 
-def test_tma_fed_xpass_matches_oracle():
-    """Schedule 4 on a ragged multi-group case against the FP64 oracle (the
-    forward parity bound of the FP32-level forms)."""
+@pytest.mark.parametrize("variant", [4, 5])
+def test_tma_fed_passes_match_oracle(variant):
+    """Schedules 4 and 5 on a ragged multi-group case against the FP64 oracle
+    (the forward parity bound of the FP32-level forms)."""
     from paper_2202_09421_gb300 import binding as B
     from paper_2202_09421_gb300.solver import FCDOMSolver
     wl = _stable_custom(100, 70, 32, 2)
     dev = torch.device("cuda:0")
     s = FCDOMSolver(wl.grid, wl.optics, torch.tensor(wl.mua, dtype=torch.float32, device=dev),
                     torch.tensor(wl.mus, dtype=torch.float32, device=dev), wl.c, wl.dt, precision=TF32X3)
-    B.rte_set_pass_variant(s.ctx, 4)
-    s.forward(wl.groups, wl.n_steps, list(wl.snap_steps))
+    B.rte_set_pass_variant(s.ctx, variant)
+    fl = s.forward(wl.groups, wl.n_steps, list(wl.snap_steps))
     curves = s.readout(wl.detectors).cpu().numpy()
     s.close()
-    ref, _, _ = oracle_forward(wl)
+    ref, f_ref, _ = oracle_forward(wl)
     assert rel_l2(curves, ref) <= 1e-5, rel_l2(curves, ref)
+    assert rel_l2(fl.cpu().numpy(), f_ref) <= 1e-5
+
+
+def test_tma_fed_ypass_adjoint_matches_one_tile_bitwise():
+    """The continuous adjoint march injects the data residual on the boundary
+    (the rho term of the y-pass epilogue) and recomputes the forward from
+    checkpoints; under schedule 5 both run the TMA-fed passes, and J and the
+    gradients equal the one-tile schedule's bit for bit."""
+    from paper_2202_09421_gb300 import binding as B
+    from paper_2202_09421_gb300.solver import FCDOMSolver
+    wl = _stable_custom(72, 64, 32, 2, n_steps=50)
+    dev = torch.device("cuda:0")
+    out = []
+    for variant in (1, 5):
+        s = FCDOMSolver(wl.grid, wl.optics, torch.tensor(wl.mua, dtype=torch.float32, device=dev),
+                        torch.tensor(wl.mus, dtype=torch.float32, device=dev), wl.c, wl.dt, precision=TF32X3,
+                        ckpt_interval=13)
+        B.rte_set_pass_variant(s.ctx, variant)
+        s.forward(wl.groups, wl.n_steps)
+        meas = 0.7 * s.readout(wl.detectors)
+        J, ga, gb = s.adjoint_gradient(wl.detectors, meas)
+        out.append((J, ga.cpu().numpy(), gb.cpu().numpy()))
+        s.close()
+    assert out[0][0] == out[1][0] and out[0][0] > 0
+    assert np.abs(out[0][1]).max() > 0
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
