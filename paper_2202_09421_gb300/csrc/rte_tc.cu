@@ -676,7 +676,11 @@ __global__ void __launch_bounds__(kThreads, MM == 64 ? 1 : 2)
     tc_pass_kernel(StepArgs a, BoundaryArgs b, float* __restrict__ U, float* __restrict__ R,
                    const float* __restrict__ L1, const float* __restrict__ L2, float* __restrict__ L3,
                    int src_step, int ring_step) {
-  tc_pass_body<XPASS, PREC, MM, SCAT_TC>(a, b, U, R, L1, L2, L3, src_step, ring_step, blockIdx.x, blockIdx.z);
+  // The y-pass walks the groups last to first: it starts on the groups whose
+  // R the x-pass wrote last (still in L2) and ends on the groups whose
+  // u^{k+1} the next x-pass reads first.
+  const int g = XPASS ? static_cast<int>(blockIdx.z) : static_cast<int>(gridDim.z - 1 - blockIdx.z);
+  tc_pass_body<XPASS, PREC, MM, SCAT_TC>(a, b, U, R, L1, L2, L3, src_step, ring_step, blockIdx.x, g);
 }
 
 // Batched form: the CTAs of one launch cover the tiles of several media
