@@ -430,10 +430,9 @@ rte_status rte_autotune(rte_ctx* ctx, const rte_source_group* groups, int n_grou
  * RTE_ERR_UNSUPPORTED.  The context (operators and medium) must come from
  * rte_init_medium, called while allocation is allowed; this call does not
  * touch the context's rte_forward results.  The first call on each device
- * looks up the array's device address (cudaGetSymbolAddress) and should
- * come before any stream capture.  Every call shares the array and finds the
- * previous call's data there (it zeroes what must start at zero); calls that
- * overlap on the GPU race on it.  Host tables are copied from pageable
+ * looks up the array's device address (cudaGetSymbolAddress).  Every call
+ * shares the array and finds the previous call's data there (it zeroes what
+ * must start at zero); calls that overlap on the GPU race on it.  Host tables are copied from pageable
  * memory, so the call returns after they have left the host.  The calling
  * thread's current device must be the context's device (the array's address
  * is looked up there).  In the tensor-core precisions the call synchronises
