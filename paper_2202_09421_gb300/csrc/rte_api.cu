@@ -1276,8 +1276,9 @@ rte_status rte_adjoint_gradient_batch(rte_ctx* const* ctxs, int n_ctx, const rte
   // Per medium: detector curves, objective, adjoint boundary data rho of eq.
   // (AdjointProblem), zeroed gradients and adjoint state (as adjoint_impl).
   int max_ncell = 0;
-  std::vector<rte_kern::GradJob> gjobs(n_ctx);
-  std::vector<rte_kern::SaveJob> sjobs(n_ctx);
+  // gradient-term and state-save jobs, one set per segment buffer
+  std::vector<rte_kern::GradJob> gjobs(2 * n_ctx);
+  std::vector<rte_kern::SaveJob> sjobs(2 * n_ctx);
   std::vector<std::vector<float>> keep_f;               // host tables alive until the copies are done
   std::vector<std::vector<int>> keep_i;
   for (int i = 0; i < n_ctx; ++i) {
@@ -1306,7 +1307,7 @@ rte_status rte_adjoint_gradient_batch(rte_ctx* const* ctxs, int n_ctx, const rte
     RTE_TRY(ensure(c->MU, gbytes));
     RTE_TRY(ensure(c->RA, gbytes));
     for (int q = 0; q < 3; ++q) RTE_TRY(ensure(c->LA[q], gbytes));
-    RTE_TRY(ensure(c->seg, static_cast<size_t>(I) * gbytes));   // one segment of recomputed states
+    RTE_TRY(ensure(c->seg, 2 * static_cast<size_t>(I) * gbytes));   // two segments of recomputed states
     const int* lo = static_cast<const int*>(c->lohi.p);
     RTE_TRY(cuda_status(rte_kern::launch_readout(F(c->ring), c->ring_len, N, G, F(c->Wd), lo, lo + n_det[i],
                                                  n_det[i], nullptr, D(c->curves64), st, &c0->launches)));
@@ -1318,20 +1319,23 @@ rte_status rte_adjoint_gradient_batch(rte_ctx* const* ctxs, int n_ctx, const rte
     RTE_TRY(cuda_status(cudaMemsetAsync(c->grad_b.p, 0, ncell * sizeof(double), st)));
     RTE_TRY(cuda_status(cudaMemsetAsync(c->MU.p, 0, gbytes, st)));
     for (int q = 0; q < 3; ++q) RTE_TRY(cuda_status(cudaMemsetAsync(c->LA[q].p, 0, gbytes, st)));
-    rte_kern::GradJob& gj = gjobs[i];
-    gj.MU = F(c->MU);
-    gj.seg = F(c->seg);
-    gj.slot_floats = gfloats;
-    gj.PT = F(c->PT);
-    gj.area = F(c->area);
-    gj.ncell = static_cast<long long>(ncell);
-    gj.M = c->M;
-    gj.G = G;
-    gj.plane = c->plane;
-    gj.scale = (2.0 * kPi / c->M) * c->par.dt;
-    gj.grad_a = (dJ_dmua && dJ_dmua[i]) ? D(c->grad_a) : nullptr;
-    gj.grad_b = (dJ_dmus && dJ_dmus[i]) ? D(c->grad_b) : nullptr;
-    sjobs[i] = rte_kern::SaveJob{F(c->U), F(c->seg), gfloats};
+    for (int bsel = 0; bsel < 2; ++bsel) {
+      float* segb = F(c->seg) + static_cast<size_t>(bsel) * I * gfloats;
+      rte_kern::GradJob& gj = gjobs[bsel * n_ctx + i];
+      gj.MU = F(c->MU);
+      gj.seg = segb;
+      gj.slot_floats = gfloats;
+      gj.PT = F(c->PT);
+      gj.area = F(c->area);
+      gj.ncell = static_cast<long long>(ncell);
+      gj.M = c->M;
+      gj.G = G;
+      gj.plane = c->plane;
+      gj.scale = (2.0 * kPi / c->M) * c->par.dt;
+      gj.grad_a = (dJ_dmua && dJ_dmua[i]) ? D(c->grad_a) : nullptr;
+      gj.grad_b = (dJ_dmus && dJ_dmus[i]) ? D(c->grad_b) : nullptr;
+      sjobs[bsel * n_ctx + i] = rte_kern::SaveJob{F(c->U), segb, gfloats};
+    }
     max_ncell = std::max(max_ncell, static_cast<int>(ncell));
   }
   // Tables of the recompute (forward boundary data, no exitance ring) and of
@@ -1375,37 +1379,64 @@ rte_status rte_adjoint_gradient_batch(rte_ctx* const* ctxs, int n_ctx, const rte
   const auto* ta_dev = static_cast<const rte_kern::BatchProblem*>(c0->batch_tab_adj.p);
   const auto* gj_dev = static_cast<const rte_kern::GradJob*>(c0->batch_jobs.p);
   const auto* sj_dev = reinterpret_cast<const rte_kern::SaveJob*>(static_cast<const char*>(c0->batch_jobs.p) + jg);
+  if (!c0->astream) {
+    RTE_TRY(cuda_status(cudaStreamCreateWithFlags(&c0->astream, cudaStreamNonBlocking)));
+    for (int k = 0; k < 4; ++k) RTE_TRY(cuda_status(cudaEventCreateWithFlags(&c0->aev[k], cudaEventDisableTiming)));
+  }
+  const cudaStream_t rs = c0->astream;
 
-  // Segments in reverse: recompute the segment's forward levels of every
-  // medium from its checkpoint (one x- and one y-pass launch per step over
-  // all media, then one launch saving every medium's state), then the
-  // adjoint steps of eq. (AdjointProblem) and their gradient terms (eq.
-  // FDwin22) for levels s_end - 1 .. s0, again one launch of each kind per
-  // level for all media.
+  // Segments in reverse order, as adjoint_impl: the forward levels of a
+  // segment are recomputed from every medium's checkpoint on a second stream
+  // (one x- and one y-pass launch per step over all media, then one launch
+  // saving every medium's state into segment buffer k % 2), overlapping the
+  // adjoint march of the segment before it in this order on the context
+  // stream (the adjoint steps of eq. (AdjointProblem) for levels s_end - 1 ..
+  // s0, one launch of each kind per level for all media, and their gradient
+  // terms, eq. FDwin22, read from the other buffer).  done_fwd[b] orders an
+  // adjoint after the recompute into b; done_adj[b] orders the next
+  // recompute into b after the adjoint that read it.
   const int last = N - 2;
-  int hl_adj = 0;
-  for (int seg = c0->n_ckpt - 1; seg >= 0; --seg) {
-    if (seg * I > last) continue;
-    const int s0 = seg * I, s_end = std::min(s0 + I, last + 1);
+  std::vector<int> segs;
+  for (int seg = c0->n_ckpt - 1; seg >= 0; --seg)
+    if (seg * I <= last) segs.push_back(seg);
+  cudaEvent_t* done_fwd = c0->aev;
+  cudaEvent_t* done_adj = c0->aev + 2;
+  RTE_TRY(cuda_status(cudaEventRecord(done_adj[0], st)));
+  RTE_TRY(cuda_status(cudaStreamWaitEvent(rs, done_adj[0], 0)));
+  auto recompute = [&](int k) -> rte_status {
+    const int s0 = segs[k] * I, s_end = std::min(s0 + I, last + 1);
     for (int i = 0; i < n_ctx; ++i) {
       rte_ctx* c = ctxs[i];
       const size_t gbytes = static_cast<size_t>(c->G) * c->plane * sizeof(float);
-      const char* base = static_cast<const char*>(c->ckpt.p) + static_cast<size_t>(seg) * 4 * gbytes;
-      RTE_TRY(cuda_status(cudaMemcpyAsync(c->U.p, base, gbytes, cudaMemcpyDeviceToDevice, st)));
+      const char* base = static_cast<const char*>(c->ckpt.p) + static_cast<size_t>(segs[k]) * 4 * gbytes;
+      RTE_TRY(cuda_status(cudaMemcpyAsync(c->U.p, base, gbytes, cudaMemcpyDeviceToDevice, rs)));
       for (int q = 0; q < 3; ++q)
-        RTE_TRY(cuda_status(cudaMemcpyAsync(c->L[q].p, base + (q + 1) * gbytes, gbytes, cudaMemcpyDeviceToDevice, st)));
+        RTE_TRY(cuda_status(cudaMemcpyAsync(c->L[q].p, base + (q + 1) * gbytes, gbytes, cudaMemcpyDeviceToDevice, rs)));
     }
     int hl = 0;
     for (int s = s0; s < s_end; ++s) {
-      RTE_TRY(cuda_status(rte_kern::launch_step_tc_batched(tf.data(), tf_dev, n_ctx, s, hl, st, &c0->launches)));
-      RTE_TRY(cuda_status(rte_kern::launch_save_batch(sj_dev, n_ctx, s - s0, st, &c0->launches)));
+      RTE_TRY(cuda_status(rte_kern::launch_step_tc_batched(tf.data(), tf_dev, n_ctx, s, hl, rs, &c0->launches)));
+      RTE_TRY(cuda_status(rte_kern::launch_save_batch(sj_dev + (k % 2) * n_ctx, n_ctx, s - s0, rs, &c0->launches)));
       hl = (hl + 2) % 3;
     }
+    return cuda_status(cudaEventRecord(done_fwd[k % 2], rs));
+  };
+  int hl_adj = 0;
+  if (!segs.empty()) RTE_TRY(recompute(0));
+  for (size_t k = 0; k < segs.size(); ++k) {
+    const int s0 = segs[k] * I, s_end = std::min(s0 + I, last + 1);
+    if (k + 1 < segs.size()) {
+      if (k >= 1) RTE_TRY(cuda_status(cudaStreamWaitEvent(rs, done_adj[(k + 1) % 2], 0)));
+      RTE_TRY(recompute(static_cast<int>(k + 1)));
+    }
+    RTE_TRY(cuda_status(cudaStreamWaitEvent(st, done_fwd[k % 2], 0)));
     for (int lvl = s_end - 1; lvl >= s0; --lvl) {
       RTE_TRY(cuda_status(rte_kern::launch_step_tc_batched(ta.data(), ta_dev, n_ctx, lvl, hl_adj, st, &c0->launches)));
       hl_adj = (hl_adj + 2) % 3;
-      RTE_TRY(cuda_status(rte_kern::launch_grad_batch(gj_dev, n_ctx, max_ncell, lvl - s0, 1, st, &c0->launches)));
+      RTE_TRY(cuda_status(rte_kern::launch_grad_batch(gj_dev + (k % 2) * n_ctx, n_ctx, max_ncell, c0->M, lvl - s0, 1,
+                                                      st, &c0->launches)));
     }
+    RTE_TRY(cuda_status(cudaEventRecord(done_adj[k % 2], st)));
   }
   for (int i = 0; i < n_ctx; ++i) {
     rte_ctx* c = ctxs[i];

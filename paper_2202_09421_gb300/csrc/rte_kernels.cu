@@ -417,8 +417,56 @@ __global__ void rho_kernel(const float* __restrict__ resid, const float* __restr
   rho[idx] = scale * acc;
 }
 
-// One warp per grid cell: the gradient terms of eq. (FDwin22) summed over the
-// groups and the ordinates (see launch_grad).
+// The gradient terms of eq. (FDwin22) at one grid cell, summed over the
+// groups and the ordinates (see launch_grad):
+//   sa = sum_g sum_m lam_m u_m,  sb = sum_g sum_m lam_m (u_m - (P~u)_m),
+// lam the adjoint field (its ordinates flipped by M/2 in the continuous form).
+// One thread per cell for M in {16, 32}: the node's M values of u and lam
+// arrive as 32-byte loads, and P~u uses the circulant's first column p_d =
+// P~[d][0] (P~[m][q] = p_{(m - q) mod M}) from registers, summed over q in
+// order for every m.
+// 32 bytes of read-only data into 8 registers (32-byte aligned address).
+__device__ __forceinline__ void ld32b(const float* ptr, float* v) {
+  asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "l"(ptr));
+}
+
+template <int MM>
+__device__ __forceinline__ void grad_node(const float* __restrict__ MU, const float* __restrict__ Useg,
+                                          const float* __restrict__ PT, const float* __restrict__ area,
+                                          long long cell, int G, size_t plane, size_t useg_gs, double scale,
+                                          int flip, double* __restrict__ grad_a, double* __restrict__ grad_b) {
+  float p[MM];
+#pragma unroll
+  for (int d = 0; d < MM; ++d) p[d] = __ldg(PT + d);            // P~[0][d] = p_d (symmetric circulant)
+  float sa = 0.f, sb = 0.f;
+  for (int g = 0; g < G; ++g) {
+    const float* u = Useg + static_cast<size_t>(g) * useg_gs + static_cast<size_t>(cell) * MM;
+    const float* mu = MU + static_cast<size_t>(g) * plane + static_cast<size_t>(cell) * MM;
+    float uu[MM], lam[MM];
+#pragma unroll
+    for (int k = 0; k < MM / 8; ++k) {
+      ld32b(u + 8 * k, uu + 8 * k);
+      ld32b(mu + 8 * k, lam + 8 * k);
+    }
+#pragma unroll
+    for (int m = 0; m < MM; ++m) {
+      float pu = 0.f;
+#pragma unroll
+      for (int q = 0; q < MM; ++q) pu = fmaf(p[(m - q + MM) % MM], uu[q], pu);
+      const float l = flip ? lam[(m + MM / 2) % MM] : lam[m];
+      sa = fmaf(l, uu[m], sa);
+      sb = fmaf(l, uu[m] - pu, sb);
+    }
+  }
+  const double k = area ? scale * static_cast<double>(area[cell]) : scale;
+  if (grad_a) grad_a[cell] -= k * static_cast<double>(sa);
+  if (grad_b) grad_b[cell] -= k * static_cast<double>(sb);
+}
+
+// Any M: one warp per cell, the lanes over the ordinates, the row of P~ from
+// memory.
 __device__ __forceinline__ void grad_cell(const float* __restrict__ MU, const float* __restrict__ Useg,
                                           const float* __restrict__ PT, const float* __restrict__ area,
                                           long long cell, int M, int G, size_t plane, size_t useg_gs,
@@ -450,11 +498,21 @@ __device__ __forceinline__ void grad_cell(const float* __restrict__ MU, const fl
   }
 }
 
+// M in {16, 32}: one thread per cell; other M: one warp per cell.
+__device__ __forceinline__ bool grad_by_thread(int M) { return M == 16 || M == 32; }
+
 __global__ void grad_kernel(const float* __restrict__ MU, const float* __restrict__ Useg,
                             const float* __restrict__ PT, const float* __restrict__ area, int ncell,
                             int M, int G, size_t plane, size_t useg_gs, double scale, int flip,
                             double* __restrict__ grad_a, double* __restrict__ grad_b) {
-  const long long cell = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (grad_by_thread(M)) {
+    if (t >= ncell) return;
+    if (M == 32) grad_node<32>(MU, Useg, PT, area, t, G, plane, useg_gs, scale, flip, grad_a, grad_b);
+    else grad_node<16>(MU, Useg, PT, area, t, G, plane, useg_gs, scale, flip, grad_a, grad_b);
+    return;
+  }
+  const long long cell = t >> 5;
   if (cell >= ncell) return;   // whole warp exits together
   grad_cell(MU, Useg, PT, area, cell, M, G, plane, useg_gs, scale, flip, grad_a, grad_b);
 }
@@ -464,10 +522,17 @@ __global__ void grad_kernel(const float* __restrict__ MU, const float* __restric
 // buffer.
 __global__ void grad_batch_kernel(const GradJob* __restrict__ jobs, int slot, int flip) {
   const GradJob& j = jobs[blockIdx.y];
-  const long long cell = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const float* useg = j.seg + static_cast<size_t>(slot) * j.slot_floats;
+  if (grad_by_thread(j.M)) {
+    if (t >= j.ncell) return;
+    if (j.M == 32) grad_node<32>(j.MU, useg, j.PT, j.area, t, j.G, j.plane, j.plane, j.scale, flip, j.grad_a, j.grad_b);
+    else grad_node<16>(j.MU, useg, j.PT, j.area, t, j.G, j.plane, j.plane, j.scale, flip, j.grad_a, j.grad_b);
+    return;
+  }
+  const long long cell = t >> 5;
   if (cell >= j.ncell) return;
-  grad_cell(j.MU, j.seg + static_cast<size_t>(slot) * j.slot_floats, j.PT, j.area, cell, j.M, j.G, j.plane,
-            j.plane, j.scale, flip, j.grad_a, j.grad_b);
+  grad_cell(j.MU, useg, j.PT, j.area, cell, j.M, j.G, j.plane, j.plane, j.scale, flip, j.grad_a, j.grad_b);
 }
 
 __global__ void save_batch_kernel(const SaveJob* __restrict__ jobs, int slot) {
@@ -475,9 +540,18 @@ __global__ void save_batch_kernel(const SaveJob* __restrict__ jobs, int slot) {
   const size_t n4 = j.n_floats / 4;
   const float4* src = reinterpret_cast<const float4*>(j.src);
   float4* dst = reinterpret_cast<float4*>(j.seg + static_cast<size_t>(slot) * j.n_floats);
-  for (size_t k = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < n4;
-       k += static_cast<size_t>(gridDim.x) * blockDim.x)
-    dst[k] = src[k];
+  // four independent 16-byte loads in flight per thread and pass
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  size_t k = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (; k + 3 * stride < n4; k += 4 * stride) {
+    const float4 v0 = __ldg(src + k), v1 = __ldg(src + k + stride), v2 = __ldg(src + k + 2 * stride),
+                 v3 = __ldg(src + k + 3 * stride);
+    dst[k] = v0;
+    dst[k + stride] = v1;
+    dst[k + 2 * stride] = v2;
+    dst[k + 3 * stride] = v3;
+  }
+  for (; k < n4; k += stride) dst[k] = __ldg(src + k);
 }
 
 __global__ void to_float_kernel(const double* in, float* out, size_t n) {
@@ -689,16 +763,18 @@ cudaError_t launch_rho(const float* resid, const float* Wn, int n_det, int ring_
   return cudaGetLastError();
 }
 
-cudaError_t launch_grad_batch(const GradJob* jobs_dev, int n_jobs, int max_ncell, int slot, int flip,
-                              cudaStream_t s, long long* launches) {
+cudaError_t launch_grad_batch(const GradJob* jobs_dev, int n_jobs, int max_ncell, int m_common, int slot,
+                              int flip, cudaStream_t s, long long* launches) {
+  // one thread per cell for M in {16, 32} (every medium of a batch shares M)
   dim3 grid((max_ncell * 32 + 255) / 256, n_jobs);
+  if (m_common == 16 || m_common == 32) grid.x = (max_ncell + 255) / 256;
   grad_batch_kernel<<<grid, 256, 0, s>>>(jobs_dev, slot, flip);
   if (launches) *launches += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_save_batch(const SaveJob* jobs_dev, int n_jobs, int slot, cudaStream_t s, long long* launches) {
-  dim3 grid(148, n_jobs);
+  dim3 grid(4 * 152, n_jobs);
   save_batch_kernel<<<grid, 256, 0, s>>>(jobs_dev, slot);
   if (launches) *launches += 1;
   return cudaGetLastError();
@@ -725,8 +801,10 @@ cudaError_t launch_grad(const float* MU, const float* Useg, const float* PT, con
                         double scale, int flip, double* grad_a, double* grad_b, cudaStream_t s,
                         long long* launches) {
   const int ncell = nx * ny;
-  grad_kernel<<<(ncell * 32 + 255) / 256, 256, 0, s>>>(MU, Useg, PT, area, ncell, M, G, plane,
-                                                        useg_group_stride, scale, flip, grad_a, grad_b);
+  const long long threads = (M == 16 || M == 32) ? ncell : 32LL * ncell;
+  grad_kernel<<<static_cast<int>((threads + 255) / 256), 256, 0, s>>>(MU, Useg, PT, area, ncell, M, G, plane,
+                                                                      useg_group_stride, scale, flip, grad_a,
+                                                                      grad_b);
   if (launches) *launches += 1;
   return cudaGetLastError();
 }

@@ -223,8 +223,9 @@ struct SaveJob {
   float* seg;
   size_t n_floats;                  // a multiple of 4
 };
-cudaError_t launch_grad_batch(const GradJob* jobs_dev, int n_jobs, int max_ncell, int slot, int flip,
-                              cudaStream_t s, long long* launches);
+// m_common: the ordinate count every job shares.
+cudaError_t launch_grad_batch(const GradJob* jobs_dev, int n_jobs, int max_ncell, int m_common, int slot,
+                              int flip, cudaStream_t s, long long* launches);
 cudaError_t launch_save_batch(const SaveJob* jobs_dev, int n_jobs, int slot, cudaStream_t s, long long* launches);
 
 cudaError_t launch_to_float(const double* in, float* out, size_t n, cudaStream_t s,
