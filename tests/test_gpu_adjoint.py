@@ -46,6 +46,31 @@ def test_adjoint_gradient_matches_oracle(ckpt):
     s.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_adjoint_gradient_m64_matches_oracle(precision):
+    """M = 64: the gradient terms take the one-warp-per-cell form (the
+    one-thread-per-cell form covers M = 16 and 32), in the plain FP32 and the
+    3xTF32 precisions."""
+    from paper_2202_09421_gb300.solver import FCDOMSolver
+    wl, meas = _setup(n=24, M=64, steps=80, ckpt=30)
+    dev = torch.device("cuda:0")
+    s = FCDOMSolver(wl.grid, wl.optics, torch.tensor(wl.mua, dtype=torch.float32, device=dev),
+                    torch.tensor(wl.mus, dtype=torch.float32, device=dev), wl.c, wl.dt,
+                    ckpt_interval=30, precision=precision)
+    s.forward(wl.groups, wl.n_steps)
+    J, ga, gb = s.adjoint_gradient(wl.detectors, torch.tensor(meas, dtype=torch.float32, device=dev))
+    s.close()
+    S = Solver(wl)
+    Jo, gao, gbo = 0.0, 0.0, 0.0
+    for k, g in enumerate(wl.groups):
+        j, a_, b_, _ = S.adjoint_gradient(g, wl.n_steps, wl.detectors, meas[k])
+        Jo, gao, gbo = Jo + j, gao + a_, gbo + b_
+    print(f"M64 prec {precision}: J {J:.6e} vs {Jo:.6e}; grad_a rel L2 {rel_l2(ga.cpu(), gao):.2e}; "
+          f"grad_b rel L2 {rel_l2(gb.cpu(), gbo):.2e}")
+    assert abs(J - Jo) < 1e-5 * abs(Jo)
+    assert rel_l2(ga.cpu(), gao) < 1e-4 and rel_l2(gb.cpu(), gbo) < 1e-4
+
+
 def test_autograd_function_backward_is_the_adjoint():
     from paper_2202_09421_gb300.solver import FCDOMSolver, RTEObjective
     wl, meas = _setup(groups=1)
