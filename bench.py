@@ -107,9 +107,9 @@ def parse():
                          "configuration), persistent warp-specialised, one-tile x-pass with the "
                          "pipelined persistent y-pass, or the TMA-fed persistent x-pass")
     ap.add_argument("--no-autotune", action="store_true", help="same as --schedule one-tile")
-    ap.add_argument("--inverse", type=int, default=0, metavar="ITERS",
+    ap.add_argument("--inverse", type=int, default=10, metavar="ITERS",
                     help="also run the inverse solver (Algorithm 2) for ITERS L-BFGS-B iterations, "
-                         "single sources against staggered groups")
+                         "single sources against staggered groups (0: skip; about 7 s at 10)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the batched (48 media) and 512^2 M=64 precision measurements")
     return ap.parse_args()
