@@ -55,6 +55,80 @@ def test_forward_tomo256_truncated():
     _compare(wl, "tomo256x60", state=False)
 
 
+def test_tomo256_bench_configuration():
+    """The benchmark's launch configuration at full size: the 256 x 256, M = 32
+    tomography medium with all 16 sources in one march, 3xTF32, the TMA-fed
+    x-pass schedule that the autotuner picks there.  (1) Over the first 60
+    steps (the oracle's bounded sample) the first and the last source's
+    curves and fluence match the oracle.  (2) Over all 2000 steps, a source's
+    curves equal a march of that source alone bit for bit: every tile's
+    arithmetic is independent of which other sources share the launch, which
+    holds at any size."""
+    from paper_2202_09421_gb300 import binding as B
+    from paper_2202_09421_gb300.solver import FCDOMSolver
+    dev = torch.device("cuda:0")
+
+    def solver(wl):
+        s = FCDOMSolver(wl.grid, wl.optics, torch.tensor(wl.mua, dtype=torch.float32, device=dev),
+                        torch.tensor(wl.mus, dtype=torch.float32, device=dev), wl.c, wl.dt,
+                        precision=B.RTE_PREC_TF32X3)
+        B.rte_set_pass_variant(s.ctx, 4)
+        return s
+
+    short = workload_tomo256(n_steps=60)
+    s = solver(short)
+    fl = s.forward(short.groups, short.n_steps, [59]).cpu().numpy()
+    curves = s.readout(short.detectors).cpu().numpy()
+    s.close()
+    ends = [short.groups[0], short.groups[-1]]
+    c_ref, f_ref, _ = oracle_forward(short, groups=ends, snaps=[59])
+    for k, gi in enumerate((0, len(short.groups) - 1)):
+        ec, ef = rel_l2(curves[gi], c_ref[k]), rel_l2(fl[gi], f_ref[k])
+        print(f"tomo256 16 sources x 60, source {gi}: curves rel L2 {ec:.3e}, fluence rel L2 {ef:.3e}")
+        assert ec <= TOL and ef <= TOL
+
+    full = workload_tomo256()
+    s = solver(full)
+    s.forward(full.groups, full.n_steps)
+    all_curves = s.readout(full.detectors).cpu().numpy()
+    s.close()
+    assert np.isfinite(all_curves).all() and all_curves.max() > 0
+    for gi in (0, 7, 15):
+        s = solver(full)
+        s.forward([full.groups[gi]], full.n_steps)
+        alone = s.readout(full.detectors).cpu().numpy()[0]
+        s.close()
+        assert np.array_equal(alone, all_curves[gi]), gi
+
+
+@pytest.mark.parametrize("case", ["isotropic", "no_scattering", "no_absorption", "matched_index"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_forward_degenerate_media(case, precision):
+    """Degenerate cases of the method against the oracle: isotropic
+    scattering (g = 0: every entry of P~ equal), no scattering (b = 0: the
+    scattering term vanishes), no absorption (a = 0), and an index-matched
+    boundary (n = 1 inside and out: the Fresnel coefficients vanish and the
+    boundary condition only injects), in plain FP32 and 3xTF32."""
+    from dataclasses import replace
+    kw = dict(L=1.0, mus=20.0, mua=0.3, n_groups=2, t_s=1.0, sigma_t=0.4)
+    if case == "isotropic":
+        kw["g"] = 0.0
+    elif case == "no_scattering":
+        kw["mus"] = 0.0
+    elif case == "no_absorption":
+        kw["mua"] = 0.0
+    wl = workload_custom(48, 40, 16, 80, 0.04, **kw)
+    if case == "matched_index":
+        wl = replace(wl, optics=replace(wl.optics, n_in=1.0), c=0.0299792458)
+    s, fl, curves = gpu_forward(wl, precision=precision)
+    s.close()
+    c_ref, f_ref, _ = oracle_forward(wl)
+    ec, ef = rel_l2(curves, c_ref), rel_l2(fl, f_ref)
+    print(f"degenerate {case} prec {precision}: curves rel L2 {ec:.3e}, fluence rel L2 {ef:.3e}")
+    assert np.abs(c_ref).max() > 0
+    assert ec <= TOL and ef <= TOL
+
+
 def test_mss_superposition_on_gpu():
     """Linearity in the source (eq. RTE): a two-beam staggered group's curves
     equal the sum of its single-beam runs."""
