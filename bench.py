@@ -62,8 +62,6 @@ NCU_TRAFFIC = {
     # TMA-fed x-pass (csrc/rte_tc_stream.cu + rte_tc_common.cuh) and the
     # one-tile y-pass (csrc/rte_tc.cu + rte_tc_common.cuh), schedule 4:
     # profiles/tc_stream_passes_tomo256_ncu.md
-    ("tc_pass_stream<x>", "21974cd08a6aab48"): 139.312640e6 + 89.435904e6,
-    ("tc_pass_kernel<y>", "fec6f20c38ec5839"): 687.358208e6 + 188.806144e6,
     # tile-local fused step (csrc/rte_fused.cu), 16 x 16 parts:
     # profiles/fused_step_tomo256_ncu_full.md
     ("fused_step_kernel", "09d63ccdc8189d08"): 538.545920e6 + 231.291136e6,

@@ -98,6 +98,8 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
 
   // A launch after a timed-out one does nothing (the march reports the error).
   if (*static_cast<volatile int*>(a.err)) return;
+  // x-pass: the y-pass that follows may be scheduled as soon as CTAs leave.
+  if (XPASS) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   unsigned char* sm = smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023);
   unsigned char* Psm = sm + L.stage_bytes;    // P~ image (x-pass, TC scattering)
   const uint32_t bar_full = smem_u32(&bars[0]), bar_done = smem_u32(&bars[1]);
@@ -248,6 +250,14 @@ __device__ __forceinline__ void tc_pass_body(const StepArgs& a, const BoundaryAr
   }
   ok = mbar_wait(bar_done, (L.n_kc - 1) & 1, a.err) && ok;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // y-pass launched as a dependent of the x-pass: its main loop read only
+  // u^k and D_y; the epilogue reads R and rewrites u, so it waits here for
+  // the x-pass to have completed (no-op for an ordinary launch).
+  if (!XPASS) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    // an x-pass wait that ran out while this CTA's main loop ran: write nothing
+    if (*static_cast<volatile int*>(a.err)) ok = false;
+  }
 
   // ---------------- x-pass: scattering contraction into the same tiles ----------------
   if constexpr (XPASS && SCAT_TC) {
@@ -711,7 +721,7 @@ __global__ void __launch_bounds__(kThreads, MM == 64 ? 1 : 2)
 
 template <bool XPASS, int PREC, int MM, bool SCAT_TC>
 cudaError_t launch_one(const StepArgs& a, const BoundaryArgs& b, float* U, float* R, const float* L1,
-                       const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s) {
+                       const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s, bool pdl) {
   using K = Kind<PREC>;
   const TcLayout L(XPASS ? a.nx : a.ny, K::X3, K::KC);
   // The y-pass epilogue reuses the stage and P~ regions for its buffers.
@@ -729,33 +739,50 @@ cudaError_t launch_one(const StepArgs& a, const BoundaryArgs& b, float* U, float
   constexpr int per_tile = kNC / MM;
   const int lines = XPASS ? a.ny : a.nx;
   dim3 grid((lines + per_tile - 1) / per_tile, 1, a.G);
-  tc_pass_kernel<XPASS, PREC, MM, SCAT_TC><<<grid, kThreads, smem, s>>>(a, b, U, R, L1, L2, L3, src_step,
-                                                                        ring_step);
-  return cudaGetLastError();
+  if (!pdl) {
+    tc_pass_kernel<XPASS, PREC, MM, SCAT_TC><<<grid, kThreads, smem, s>>>(a, b, U, R, L1, L2, L3, src_step,
+                                                                          ring_step);
+    return cudaGetLastError();
+  }
+  // programmatic dependent launch: may start while the preceding x-pass's
+  // last CTAs run (see the wait before the y epilogue)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr_pdl[1];
+  attr_pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr_pdl[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr_pdl;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, tc_pass_kernel<XPASS, PREC, MM, SCAT_TC>, a, b, U, R, L1, L2, L3, src_step,
+                            ring_step);
 }
 
 template <bool XPASS, int PREC>
 cudaError_t launch_pass(const StepArgs& a, const BoundaryArgs& b, float* U, float* R, const float* L1,
-                        const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s) {
+                        const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s, bool pdl) {
   constexpr bool kScatOk = XPASS && !Kind<PREC>::BF;   // TC scattering: TF32 operands, M <= 32
   const bool st = kScatOk && a.tc_scatter != 0;
   if (a.M == 16)
-    return st ? launch_one<XPASS, PREC, 16, kScatOk>(a, b, U, R, L1, L2, L3, src_step, ring_step, s)
-              : launch_one<XPASS, PREC, 16, false>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
+    return st ? launch_one<XPASS, PREC, 16, kScatOk>(a, b, U, R, L1, L2, L3, src_step, ring_step, s, pdl)
+              : launch_one<XPASS, PREC, 16, false>(a, b, U, R, L1, L2, L3, src_step, ring_step, s, pdl);
   if (a.M == 32)
-    return st ? launch_one<XPASS, PREC, 32, kScatOk>(a, b, U, R, L1, L2, L3, src_step, ring_step, s)
-              : launch_one<XPASS, PREC, 32, false>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
-  return launch_one<XPASS, PREC, 64, false>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
+    return st ? launch_one<XPASS, PREC, 32, kScatOk>(a, b, U, R, L1, L2, L3, src_step, ring_step, s, pdl)
+              : launch_one<XPASS, PREC, 32, false>(a, b, U, R, L1, L2, L3, src_step, ring_step, s, pdl);
+  return launch_one<XPASS, PREC, 64, false>(a, b, U, R, L1, L2, L3, src_step, ring_step, s, pdl);
 }
 
 template <bool XPASS>
 cudaError_t launch_mode(const StepArgs& a, const BoundaryArgs& b, float* U, float* R, const float* L1,
-                        const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s) {
+                        const float* L2, float* L3, int src_step, int ring_step, cudaStream_t s,
+                        bool pdl = false) {
   switch (a.tc_mode) {
-    case 1: return launch_pass<XPASS, 1>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
-    case 2: return launch_pass<XPASS, 2>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
-    case 3: return launch_pass<XPASS, 3>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
-    default: return launch_pass<XPASS, 4>(a, b, U, R, L1, L2, L3, src_step, ring_step, s);
+    case 1: return launch_pass<XPASS, 1>(a, b, U, R, L1, L2, L3, src_step, ring_step, s, pdl);
+    case 2: return launch_pass<XPASS, 2>(a, b, U, R, L1, L2, L3, src_step, ring_step, s, pdl);
+    case 3: return launch_pass<XPASS, 3>(a, b, U, R, L1, L2, L3, src_step, ring_step, s, pdl);
+    default: return launch_pass<XPASS, 4>(a, b, U, R, L1, L2, L3, src_step, ring_step, s, pdl);
   }
 }
 
@@ -778,8 +805,22 @@ cudaError_t launch_batched_one(const BatchProblem* probs, const BatchProblem* de
                          232448 - 2048);
     attr = true;
   }
-  tc_pass_batched<XPASS, PREC, MM, SCAT_TC><<<ctas, kThreads, smem, s>>>(dev, n, step, hl);
-  return cudaGetLastError();
+  if (XPASS) {
+    tc_pass_batched<XPASS, PREC, MM, SCAT_TC><<<ctas, kThreads, smem, s>>>(dev, n, step, hl);
+    return cudaGetLastError();
+  }
+  // the y-pass as a programmatic dependent of the batched x-pass before it
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr_pdl[1];
+  attr_pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr_pdl[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr_pdl;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, tc_pass_batched<XPASS, PREC, MM, SCAT_TC>, dev, n, step, hl);
 }
 
 template <bool XPASS, int PREC>
@@ -865,7 +906,7 @@ cudaError_t launch_step_tc(const StepArgs& a, const BoundaryArgs& b, float* U, f
   e = ws        ? launch_pass_ws(false, a, b, U, R, L1, L2, L3, step, ring_step, s)
       : pipe    ? launch_ypass_pipe(a, b, U, R, L1, L2, L3, step, ring_step, s)
       : ystream ? launch_ypass_stream(a, b, U, R, L1, L2, L3, step, ring_step, s)
-                : launch_mode<false>(a, b, U, R, L1, L2, L3, step, ring_step, s);
+                : launch_mode<false>(a, b, U, R, L1, L2, L3, step, ring_step, s, !ev);
   if (ev) cudaEventRecord(ev[2], s);
   if (launches) *launches += 2;
   return e;

@@ -141,6 +141,8 @@ __global__ void __launch_bounds__(kStThreads, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // A launch after a timed-out one does nothing (the march reports the error).
   if (*static_cast<volatile int*>(a.err)) return;
+  // x-pass: the y-pass that follows may be scheduled as soon as CTAs leave.
+  if (XPASS) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int acc_cols = L.nrows_img;                 // one accumulator: n_mt * 128 columns
   unsigned char* sm = smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023);
   unsigned char* raw = sm + static_cast<size_t>(S) * L.stage_bytes;
