@@ -62,6 +62,11 @@ NCU_TRAFFIC = {
     # TMA-fed x-pass (csrc/rte_tc_stream.cu + rte_tc_common.cuh) and the
     # one-tile y-pass (csrc/rte_tc.cu + rte_tc_common.cuh), schedule 4:
     # profiles/tc_stream_passes_tomo256_ncu.md
+    # TMA-fed x-pass (csrc/rte_tc_stream.cu + rte_tc_common.cuh) and the
+    # one-tile y-pass (csrc/rte_tc.cu + rte_tc_common.cuh), schedule 4:
+    # profiles/tc_stream_passes_tomo256_ncu.md
+    ("tc_pass_stream<x>", "1eb1154312966384"): 138.943232e6 + 90.579968e6,
+    ("tc_pass_kernel<y>", "5ad975b3d17dce21"): 687.169280e6 + 188.580352e6,
     # tile-local fused step (csrc/rte_fused.cu), 16 x 16 parts:
     # profiles/fused_step_tomo256_ncu_full.md
     ("fused_step_kernel", "09d63ccdc8189d08"): 538.545920e6 + 231.291136e6,
