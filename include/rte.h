@@ -107,6 +107,17 @@ typedef struct rte_optics {
  * with rte_photon_balance).  One extra reduction launch per step, reading
  * the state once. */
 #define RTE_FLAG_PHOTON_BALANCE 4
+/* RTE_FLAG_TC_FUSED_STEP runs schedule 3 (the tile-local fused step of the
+ * decomposed operator, Sec. 4.4) with its three contractions on the tensor
+ * cores: the segment derivatives along x and y and the scattering sum as
+ * tcgen05 MMAs with split 3xTF32 operands, the AB4 update, boundary
+ * condition and exitance as in the FP32 form.  Requires RTE_PREC_TF32X3,
+ * M = 32 and fc_parts_x, fc_parts_y >= 2 with every part owning exactly 16
+ * points (else UNSUPPORTED at creation).  Without it schedule 3 runs the
+ * FP32 form, which measured faster on GB300 (0.275 against 0.39-0.44 ms per
+ * step at 256^2, M = 32, 16 x 16 parts, 16 groups): the form's 108 MMAs per
+ * subdomain have N = 16 or 32 and cost more than the FMAs they replace. */
+#define RTE_FLAG_TC_FUSED_STEP 8
 /* fc_parts_x, fc_parts_y: the subdomain decomposition of Sec. 4.4 /
  * Algorithm 1 along each axis (0 or 1: one domain).  With P parts the n
  * points of a line are split into P owned ranges [k n / P, (k + 1) n / P);
@@ -356,7 +367,8 @@ long long rte_graph_captures(const rte_ctx* ctx);
  *      Algorithm 1): one launch per step, one CTA per subdomain and group,
  *      the whole step (segment derivatives, scattering, AB4, boundary
  *      condition, exitance) in shared memory with FP32 arithmetic, in every
- *      precision; where supported (fc_parts_x, fc_parts_y >= 2 with owned
+ *      precision (with RTE_FLAG_TC_FUSED_STEP: its contractions on the
+ *      tensor cores); where supported (fc_parts_x, fc_parts_y >= 2 with owned
  *      ranges of at most 16 points, M in {16, 32}) by rte_forward and
  *      rte_adjoint_gradient (rte_discrete_adjoint_gradient and the batched
  *      and allocation-free forwards run the one-tile-per-CTA passes);

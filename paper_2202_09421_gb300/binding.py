@@ -22,6 +22,7 @@ RTE_PREC_BF16 = 4      # tcgen05 kind::f16, one BF16 product
 RTE_FLAG_TC_SCATTER = 1  # x-pass scattering as a tcgen05 contraction
 RTE_FLAG_CUDA_GRAPH = 2  # forward march captured and replayed as a CUDA graph
 RTE_FLAG_PHOTON_BALANCE = 4  # record the FP64 photon-balance terms of every step
+RTE_FLAG_TC_FUSED_STEP = 8  # schedule 3's contractions on the tensor cores (3xTF32, M = 32, 16-point parts)
 
 
 class RteGrid(ctypes.Structure):

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "_lib", "librte_fcdom.so")
 SOURCES = ["rte_setup.cpp", "rte_kernels.cu", "rte_tc.cu", "rte_tc_ws.cu", "rte_tc_pipe.cu", "rte_tc_stream.cu",
-           "rte_fused.cu", "rte_api.cu"]
+           "rte_fused.cu", "rte_fused_tc.cu", "rte_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -41,6 +41,7 @@ struct rte_ctx {
   // tile-local fused step (decomposed operators): per-part ranges and the
   // packed segment operators of each axis
   DevBuf fxp, fyp, FxT, FyT;
+  DevBuf FxImg, FyImg;             // the same as tensor-core operand images (16-point parts)
   int fused_own_max = 0;
   bool fused_exact = true;          // every part owns kFusedOwnMax points
   int tc_mode = 0;                 // the precision: 0 SIMT FP32, 1-4 tcgen05 forms
@@ -184,6 +185,8 @@ rte_kern::StepArgs step_args(rte_ctx* c, int G) {
   a.fyp = static_cast<const int*>(c->fyp.p);
   a.FxT = F(c->FxT);
   a.FyT = F(c->FyT);
+  a.FxImg = F(c->FxImg);
+  a.FyImg = F(c->FyImg);
   a.fused_own_max = c->fused_own_max;
   a.fused_exact = c->fused_exact ? 1 : 0;
   a.err = static_cast<int*>(c->err.p);
@@ -279,8 +282,9 @@ rte_status march(rte_ctx* c, DevBuf& U, DevBuf& R, DevBuf* L, int& hl, int G, in
       ev = &c->events[3 * c->n_timed++];
     }
     if (fused) {
-      RTE_TRY(cuda_status(rte_kern::launch_step_fused(a, b, cur, oth, L1, L2, L3, s, c->stream,
-                                                      &c->launches, ev)));
+      const auto step_fn = rte_kern::fused_tc_supported(a) ? rte_kern::launch_step_fused_tc
+                                                           : rte_kern::launch_step_fused;
+      RTE_TRY(cuda_status(step_fn(a, b, cur, oth, L1, L2, L3, s, c->stream, &c->launches, ev)));
       std::swap(cur, oth);
     } else {
       RTE_TRY(cuda_status(rte_kern::launch_step(a, b, cur, F(R), L1, L2, L3, s, c->stream,
@@ -700,7 +704,7 @@ rte_status rte_destroy(rte_ctx* c) {
                    &c->LA[1], &c->LA[2], &c->seg, &c->curves64, &c->resid, &c->partial,
                    &c->Jdev, &c->rho, &c->grad_a, &c->grad_b, &c->Wd, &c->Wn, &c->lohi,
                    &c->DxImg, &c->DyImg, &c->PImg, &c->DxTt, &c->DyTt, &c->DxImgT, &c->DyImgT,
-                   &c->bct_src, &c->bct_f, &c->fxp, &c->fyp, &c->FxT, &c->FyT};
+                   &c->bct_src, &c->bct_f, &c->fxp, &c->fyp, &c->FxT, &c->FyT, &c->FxImg, &c->FyImg};
   for (DevBuf* b : all) release(*b);
   release(c->batch_tab);
   release(c->batch_tab_adj);
@@ -747,7 +751,7 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
   if (g->nx > 512 || g->ny > 512 || g->M > 64) return RTE_ERR_UNSUPPORTED;
   if (!(g->xmax > g->xmin) || !(g->ymax > g->ymin)) return RTE_ERR_INVALID_ARG;
   if (!(p->dt > 0) || !(o->c > 0) || !(o->n_in > 0) || !(o->n_out > 0) || std::fabs(o->g) >= 1.0 ||
-      p->ckpt_interval < 0 || (p->flags & ~(RTE_FLAG_TC_SCATTER | RTE_FLAG_CUDA_GRAPH | RTE_FLAG_PHOTON_BALANCE)) != 0 ||
+      p->ckpt_interval < 0 || (p->flags & ~(RTE_FLAG_TC_SCATTER | RTE_FLAG_CUDA_GRAPH | RTE_FLAG_PHOTON_BALANCE | RTE_FLAG_TC_FUSED_STEP)) != 0 ||
       p->precision < RTE_PREC_FP32 || p->precision > RTE_PREC_BF16 || p->fc_parts_x < 0 || p->fc_parts_y < 0)
     return RTE_ERR_INVALID_ARG;
   if (p->precision != RTE_PREC_FP32 && !rte_kern::tc_supported(g->nx, g->ny, g->M, p->precision, p->flags))
@@ -778,7 +782,7 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
   const int parts[2] = {p->fc_parts_x, p->fc_parts_y};
   DevBuf* dst[2] = {&c->DxT, &c->DyT};
   std::vector<int> part_tab[2];
-  std::vector<float> seg_ops[2];
+  std::vector<float> seg_ops[2], seg_img[2];
   for (int ax = 0; ax < 2; ++ax) {
     const int n = dims[ax];
     if (!rte_setup::fc_derivative_matrix_parts(n, hs[ax], p->filter_alpha, p->filter_beta, parts[ax], Dm))
@@ -791,6 +795,7 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
       constexpr int kO = rte_kern::kFusedOwnMax, kS = kO + 4;
       part_tab[ax].assign(4 * parts[ax], 0);
       seg_ops[ax].assign(static_cast<size_t>(parts[ax]) * kS * kO, 0.f);
+      seg_img[ax].assign(static_cast<size_t>(parts[ax]) * 2 * kO * 32, 0.f);
       for (int k = 0; k < parts[ax]; ++k) {
         int lo, hi, slo, shi;
         rte_setup::part_range(n, parts[ax], k, lo, hi, slo, shi);
@@ -803,14 +808,22 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
           for (int i = 0; i < hi - lo; ++i)
             seg_ops[ax][(static_cast<size_t>(k) * kS + kk) * kO + i] =
                 static_cast<float>(Dm[static_cast<size_t>(lo + i) * n + slo + kk]);
+        rte_setup::tc_segment_image(Dm, n, lo, hi, slo, shi, seg_img[ax].data() + static_cast<size_t>(k) * 2 * kO * 32);
       }
     }
   }
+  if ((p->flags & RTE_FLAG_TC_FUSED_STEP) && (parts[0] < 2 || parts[1] < 2)) return fail(RTE_ERR_UNSUPPORTED);
   if (parts[0] >= 2 && parts[1] >= 2) {
     rte_status s = upload(c->fxp, part_tab[0], c->stream);
     if (s == RTE_OK) s = upload(c->fyp, part_tab[1], c->stream);
     if (s == RTE_OK) s = upload(c->FxT, seg_ops[0], c->stream);
     if (s == RTE_OK) s = upload(c->FyT, seg_ops[1], c->stream);
+    // operand images of the tensor-core fused step (3xTF32, M = 32, 16-point parts)
+    if (s == RTE_OK && (p->flags & RTE_FLAG_TC_FUSED_STEP)) {
+      if (!c->fused_exact || p->precision != RTE_PREC_TF32X3 || g->M != 32) s = RTE_ERR_UNSUPPORTED;
+      if (s == RTE_OK) s = upload(c->FxImg, seg_img[0], c->stream);
+      if (s == RTE_OK) s = upload(c->FyImg, seg_img[1], c->stream);
+    }
     if (s == RTE_OK) s = cuda_status(cudaStreamSynchronize(c->stream));
     if (s != RTE_OK) return fail(s);
   }
@@ -848,6 +861,7 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
   if (s == RTE_OK) s = upload(c->trig, trig, c->stream);
   if (s == RTE_OK) s = cuda_status(cudaMemsetAsync(c->err.p, 0, sizeof(int), c->stream));
   if (s == RTE_OK && c->tc_mode != 0 && (p->flags & RTE_FLAG_TC_SCATTER)) s = ensure_phase_image(c);
+  if (s == RTE_OK && c->FxImg.p) s = ensure_phase_image(c);   // the tensor-core fused step's scattering operand
   if (s == RTE_OK) s = upload(c->PT, PTf, c->stream);
   if (s == RTE_OK) s = upload(c->xi, xi, c->stream);
   if (s == RTE_OK) s = upload(c->eta, eta, c->stream);
@@ -1202,8 +1216,9 @@ static rte_status adjoint_impl(rte_ctx* c, const rte_detector* dets, int n_det, 
       float* L2 = F(c->LA[(hl_adj + 1) % 3]);
       float* L3 = F(c->LA[(hl_adj + 2) % 3]);
       if (fused_adj) {
-        RTE_TRY(cuda_status(rte_kern::launch_step_fused(sa, ba, mcur, moth, L1, L2, L3, lvl, c->stream,
-                                                        &c->launches)));
+        const auto step_fn = rte_kern::fused_tc_supported(sa) ? rte_kern::launch_step_fused_tc
+                                                              : rte_kern::launch_step_fused;
+        RTE_TRY(cuda_status(step_fn(sa, ba, mcur, moth, L1, L2, L3, lvl, c->stream, &c->launches, nullptr)));
         std::swap(mcur, moth);
         hl_adj = (hl_adj + 2) % 3;
       } else if (!discrete) {

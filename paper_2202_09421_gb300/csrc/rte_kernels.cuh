@@ -73,6 +73,11 @@ struct StepArgs {
   const int* fyp;
   const float* FxT;
   const float* FyT;
+  // The same segment operators as tensor-core B operands (3xTF32 split,
+  // swizzled, indexed by box position): [part][hi, lo][16 rows][32], M = 32
+  // and 16-point parts only; null otherwise.
+  const float* FxImg;
+  const float* FyImg;
   int fused_own_max;                // largest owned range over both axes
   int fused_exact;                  // every part owns exactly kFusedOwnMax points
   // The context's timeout word (device int): a tensor-core pass whose
@@ -154,9 +159,15 @@ cudaError_t launch_ypass_stream(const StepArgs& a, const BoundaryArgs& b, float*
 // ranges <= kFusedOwnMax, M in {16, 32}); reads u^k from Uin and writes
 // u^{k+1} to Uout (different buffers).
 bool fused_supported(const StepArgs& a);
+// Tensor-core form of the same step (rte_fused_tc.cu): precision 3xTF32,
+// M = 32, every part owning 16 x 16 points.
+bool fused_tc_supported(const StepArgs& a);
 cudaError_t launch_step_fused(const StepArgs& a, const BoundaryArgs& b, const float* Uin, float* Uout,
                               const float* L1, const float* L2, float* L3, int step, cudaStream_t s,
                               long long* launches, cudaEvent_t* ev = nullptr);
+cudaError_t launch_step_fused_tc(const StepArgs& a, const BoundaryArgs& b, const float* Uin, float* Uout,
+                                 const float* L1, const float* L2, float* L3, int step, cudaStream_t s,
+                                 long long* launches, cudaEvent_t* ev = nullptr);
 
 // Phi[g][j][i] = w sum_m u_m  (eq. photondensity).
 cudaError_t launch_fluence(const float* U, float* out, size_t out_group_stride, int nx, int ny,

@@ -190,6 +190,22 @@ void tc_phase_image(const std::vector<double>& P, int M, std::vector<float>& img
     }
 }
 
+void tc_segment_image(const std::vector<double>& D, int n, int lo, int hi, int slo, int shi, float* img) {
+  std::fill(img, img + 2 * 16 * 32, 0.f);
+  const int off = slo - lo + 2;
+  for (int i = 0; i < hi - lo && i < 16; ++i)
+    for (int s = 0; s < shi - slo; ++s) {
+      const int p = s + off;
+      if (p < 0 || p >= 32) continue;
+      const double v = D[static_cast<size_t>(lo + i) * n + slo + s];
+      const float h = tf32_round(static_cast<float>(v));
+      const float l = tf32_round(static_cast<float>(v - static_cast<double>(h)));
+      const size_t pos = static_cast<size_t>(i) * 32 + (((p >> 2) ^ (i & 7)) << 2) + (p & 3);
+      img[pos] = h;
+      img[16 * 32 + pos] = l;
+    }
+}
+
 double fc_spectral_radius(int n, double h, double alpha, double beta) {
   const int Np = smooth5(n + FC_C);
   const int kmax = (Np - 1) / 2;

@@ -49,6 +49,14 @@ void tc_operator_image_bf16(const std::vector<double>& D, int n, std::vector<uns
 // rows m, K = q, 32 x 32 (zero-padded) hi tile then lo tile.
 void tc_phase_image(const std::vector<double>& P, int M, std::vector<float>& img);
 
+// Segment operator of one part of the decomposed operator (Sec. 4.4) as the
+// B operand of the tensor-core fused step: rows i < hi - lo (owned points),
+// K = box position p = s + (slo - lo + 2) for segment point s < shi - slo
+// (the box starts two points before the owned range), 16 rows x 32 tf32 in
+// the K-major 128-byte-swizzle order, a hi tile then a lo tile (1024 floats
+// written to img); entries outside the segment are zero.
+void tc_segment_image(const std::vector<double>& D, int n, int lo, int hi, int slo, int shi, float* img);
+
 // Largest |multiplier| of the filtered periodic derivative on N_p points,
 // the spectral-radius estimate of D used by the stability check.
 double fc_spectral_radius(int n, double h, double alpha, double beta);

@@ -133,3 +133,95 @@ def test_fused_graph_replay_and_fallback():
     u_b = s.state(0).cpu().numpy()
     s.close()
     assert np.array_equal(u_a, u_b)
+
+
+# Tensor-core form (RTE_FLAG_TC_FUSED_STEP: 3xTF32, M = 32, every part
+# owning 16 x 16 points).
+TC_CASES = [(64, 64, (4, 4)), (96, 80, (6, 5))]
+
+
+@pytest.mark.parametrize("nx,ny,parts", TC_CASES)
+def test_fused_step_tensor_cores_matches_oracle(nx, ny, parts):
+    """The tensor-core fused step against the oracle with the same
+    decomposition (curves, fluence snapshots and the state of every group,
+    beams on every face), and against the FP32 fused step."""
+    wl = workload_custom(nx, ny, 32, 120, 0.04, L=(nx - 1) / 66, mus=20.0, n_groups=3, t_s=1.0, sigma_t=0.4)
+    from paper_2202_09421_gb300 import binding as B
+    s = _solver(wl, parts, precision=1, flags=B.RTE_FLAG_TC_FUSED_STEP)
+    launches0 = s.kernel_launches()
+    fl, curves, states = _run(s, wl)
+    launches = s.kernel_launches() - launches0
+    s.close()
+    s = _solver(wl, parts, precision=0)
+    fl0, curves0, states0 = _run(s, wl)
+    s.close()
+    S = Solver(wl, fc_parts=parts)
+    outs = [S.forward(g, wl.n_steps, wl.detectors, snap_steps=list(wl.snap_steps)) for g in wl.groups]
+    c_ref = np.stack([o["curves"] for o in outs])
+    f_ref = np.stack([[o["fluence"][k] for k in wl.snap_steps] for o in outs])
+    u_ref = np.stack([np.moveaxis(o["u"], 0, -1) for o in outs])
+    ec, ef, eu = rel_l2(curves, c_ref), rel_l2(fl, f_ref), rel_l2(states, u_ref)
+    d32 = rel_l2(states, states0)
+    print(f"fused tc {nx}x{ny} parts {parts}: curves {ec:.2e}, fluence {ef:.2e}, state {eu:.2e}; "
+          f"vs FP32 fused {d32:.2e}; {launches} launches")
+    assert ec <= 1e-5 and ef <= 1e-5 and eu <= 1e-5
+    assert d32 <= 2e-6 and rel_l2(curves, curves0) <= 2e-6
+    # the per-node maximum error stays at FP32 level too
+    assert np.max(np.abs(states - u_ref)) <= 1e-5 * np.max(np.abs(u_ref))
+    assert launches <= wl.n_steps + len(wl.snap_steps) + 2
+
+
+def test_fused_step_tensor_cores_adjoint_and_replay():
+    """Checkpointed continuous adjoint through the tensor-core fused step
+    (recompute and adjoint march) against the 3xTF32 two-pass form of the
+    same decomposed operator and the oracle; CUDA-graph replay of the march
+    equals the direct launches bit for bit."""
+    from paper_2202_09421_gb300 import binding as B
+    wl = workload_custom(64, 64, 32, 90, 0.04, L=63 / 66, mus=20.0, n_groups=2, t_s=1.0, sigma_t=0.4)
+    tgt = workload_custom(64, 64, 32, 90, 0.04, L=63 / 66, mus=20.0, n_groups=2, t_s=1.0, sigma_t=0.4, seed=7)
+    meas = np.stack([Solver(tgt, fc_parts=(4, 4)).forward(g, 90, tgt.detectors)["curves"]
+                     for g in tgt.groups]) * 0.8
+    res = {}
+    for variant in (FUSED, 1):
+        s = _solver(wl, (4, 4), precision=1, ckpt=11, variant=variant, flags=B.RTE_FLAG_TC_FUSED_STEP)
+        s.forward(wl.groups, wl.n_steps)
+        m = torch.tensor(meas, dtype=torch.float32, device=s.device)
+        res[variant] = s.adjoint_gradient(wl.detectors, m)
+        s.close()
+    S = Solver(wl, fc_parts=(4, 4))
+    Jo, gao = 0.0, 0.0
+    for k, g in enumerate(wl.groups):
+        j, a_, _, _ = S.adjoint_gradient(g, wl.n_steps, wl.detectors, meas[k])
+        Jo, gao = Jo + j, gao + a_
+    Jf, gaf, gbf = res[FUSED]
+    J2, ga2, gb2 = res[1]
+    print(f"fused tc adjoint: J {Jf:.6e} / {J2:.6e} / oracle {Jo:.6e}; grad_a vs two-pass "
+          f"{rel_l2(gaf.cpu(), ga2.cpu()):.2e}, vs oracle {rel_l2(gaf.cpu(), gao):.2e}")
+    assert abs(Jf - Jo) < 1e-5 * abs(Jo)
+    assert rel_l2(gaf.cpu(), ga2.cpu()) < 1e-5 and rel_l2(gbf.cpu(), gb2.cpu()) < 1e-5
+    assert rel_l2(gaf.cpu(), gao) < 1e-4
+
+    wl = workload_custom(64, 64, 32, 37, 0.04, L=63 / 66, mus=20.0, n_groups=1, t_s=1.0, sigma_t=0.4)
+    s = _solver(wl, (4, 4), precision=1, flags=B.RTE_FLAG_TC_FUSED_STEP)
+    _, c0, u0 = _run(s, wl)
+    s.close()
+    s = _solver(wl, (4, 4), precision=1, flags=B.RTE_FLAG_CUDA_GRAPH | B.RTE_FLAG_TC_FUSED_STEP)
+    _run(s, wl)
+    _, c1, u1 = _run(s, wl)
+    assert s.graph_captures() == 1
+    s.close()
+    assert np.array_equal(c0, c1) and np.array_equal(u0, u1)
+
+
+def test_fused_step_tensor_cores_refused_outside_its_domain():
+    """RTE_FLAG_TC_FUSED_STEP outside 3xTF32, M = 32 and 16-point parts is
+    refused at creation."""
+    from paper_2202_09421_gb300 import binding as B
+    ok = workload_custom(64, 64, 32, 10, 0.04, L=63 / 66, mus=20.0, n_groups=1, t_s=1.0, sigma_t=0.4)
+    ragged = workload_custom(48, 46, 32, 10, 0.04, L=47 / 66, mus=20.0, n_groups=1, t_s=1.0, sigma_t=0.4)
+    m16 = workload_custom(64, 64, 16, 10, 0.04, L=63 / 66, mus=20.0, n_groups=1, t_s=1.0, sigma_t=0.4)
+    for wl, parts, prec in ((ok, (4, 4), 0), (ok, (1, 1), 1), (ragged, (3, 3), 1), (m16, (4, 4), 1)):
+        with pytest.raises(B.RTEError) as err:
+            _solver(wl, parts, precision=prec, flags=B.RTE_FLAG_TC_FUSED_STEP)
+        assert err.value.status == 7             # RTE_ERR_UNSUPPORTED
+    _solver(ok, (4, 4), precision=1, flags=B.RTE_FLAG_TC_FUSED_STEP).close()
