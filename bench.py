@@ -70,6 +70,9 @@ NCU_TRAFFIC = {
     # tile-local fused step (csrc/rte_fused.cu), 16 x 16 parts:
     # profiles/fused_step_tomo256_ncu_full.md
     ("fused_step_kernel", "09d63ccdc8189d08"): 538.545920e6 + 231.291136e6,
+    # its tensor-core form (csrc/rte_fused_tc.cu + rte_tc_common.cuh):
+    # profiles/fused_step_tc_tomo256_ncu.md
+    ("fused_step_tc_kernel", "36c1cad1904e669a"): 540.756736e6 + 231.811840e6,
 }
 
 
