@@ -225,3 +225,59 @@ def test_fused_step_tensor_cores_refused_outside_its_domain():
             _solver(wl, parts, precision=prec, flags=B.RTE_FLAG_TC_FUSED_STEP)
         assert err.value.status == 7             # RTE_ERR_UNSUPPORTED
     _solver(ok, (4, 4), precision=1, flags=B.RTE_FLAG_TC_FUSED_STEP).close()
+
+
+def test_fused_steps_tomo256_bench_configuration():
+    """Both fused forms in the benchmark's launch configuration at full size:
+    the 256 x 256, M = 32 tomography medium with 16 x 16 parts and all 16
+    sources in one march (the FP32 form, and the tensor-core form with
+    RTE_FLAG_TC_FUSED_STEP).  (1) Over the first 40 steps (the oracle's
+    bounded sample) the first and the last source's curves, fluence and
+    state match the oracle with the same decomposition.  (2) Over all 2000
+    steps a source's curves equal a march of that source alone bit for bit
+    (every subdomain's arithmetic is independent of the other sources in the
+    launch), which holds at any size."""
+    from paper_2202_09421_gb300 import binding as B
+    from paper_2202_09421_gb300.solver import FCDOMSolver
+    from rte_inputs import workload_tomo256
+    dev = torch.device("cuda:0")
+    forms = {"fp32": (0, 0), "tensor cores": (1, B.RTE_FLAG_TC_FUSED_STEP)}
+
+    def solver(wl, prec, flags):
+        s = FCDOMSolver(wl.grid, wl.optics, torch.tensor(wl.mua, dtype=torch.float32, device=dev),
+                        torch.tensor(wl.mus, dtype=torch.float32, device=dev), wl.c, wl.dt, precision=prec,
+                        fc_parts=(16, 16), flags=flags)
+        B.rte_set_pass_variant(s.ctx, FUSED)
+        return s
+
+    short = workload_tomo256(n_steps=40)
+    S = Solver(short, fc_parts=(16, 16))
+    ends = (0, len(short.groups) - 1)
+    ref = {gi: S.forward(short.groups[gi], short.n_steps, short.detectors, snap_steps=[39]) for gi in ends}
+    for name, (prec, flags) in forms.items():
+        s = solver(short, prec, flags)
+        fl = s.forward(short.groups, short.n_steps, [39]).cpu().numpy()
+        curves = s.readout(short.detectors).cpu().numpy()
+        states = [s.state(gi).cpu().numpy() for gi in ends]
+        s.close()
+        for k, gi in enumerate(ends):
+            o = ref[gi]
+            ec, ef = rel_l2(curves[gi], o["curves"]), rel_l2(fl[gi][0], o["fluence"][39])
+            eu = rel_l2(states[k], np.moveaxis(o["u"], 0, -1))
+            print(f"fused {name}, tomo256 16x16 parts, 16 sources x 40, source {gi}: curves {ec:.2e}, "
+                  f"fluence {ef:.2e}, state {eu:.2e}")
+            assert ec <= 1e-5 and ef <= 1e-5 and eu <= 1e-5
+
+    full = workload_tomo256()
+    for name, (prec, flags) in forms.items():
+        s = solver(full, prec, flags)
+        s.forward(full.groups, full.n_steps)
+        all_curves = s.readout(full.detectors).cpu().numpy()
+        s.close()
+        assert np.isfinite(all_curves).all() and all_curves.max() > 0
+        for gi in (0, 9):
+            s = solver(full, prec, flags)
+            s.forward([full.groups[gi]], full.n_steps)
+            alone = s.readout(full.detectors).cpu().numpy()[0]
+            s.close()
+            assert np.array_equal(alone, all_curves[gi]), (name, gi)
