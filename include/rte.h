@@ -167,11 +167,16 @@ typedef struct rte_ctx rte_ctx;
  * (Sec. 4.1), the Fresnel/reflection tables of eq. (RTE) and the stability
  * estimate, and copies mua/mus ([ny][nx] device FP32, the paper's a and b).
  * cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ * The context belongs to the CUDA device current at this call.  A process
+ * drives one GPU (one process per GPU, as torch.distributed launches them):
+ * the kernels' shared-memory limits are set once per process, so creating a
+ * context on a second device in the same process is refused.
  * dx and dy may differ; each axis gets its own operator.
  * Errors: INVALID_ARG (null pointers, M odd or not a multiple of 8, sizes
  * below 16, unknown precision or flags), UNSUPPORTED (nx or ny above 512, M
  * above 64; a tensor-core precision with M not in {16, 32, 64} or a flag it
- * does not support), UNSTABLE_DT, OOM, CUDA. */
+ * does not support; a device other than the one of this process's first
+ * context), UNSTABLE_DT, OOM, CUDA. */
 rte_status rte_init_medium(rte_ctx** ctx, const rte_grid* grid,
                            const float* mua, const float* mus,
                            const rte_optics* optics, const rte_params* params,

@@ -1,6 +1,7 @@
 // C ABI of the FC-DOM library (include/rte.h): context, set-up uploads, the
 // time-march driver, detector readout and the checkpointed adjoint gradient.
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cmath>
 #include <cstring>
@@ -91,6 +92,8 @@ namespace {
 
 // Last CUDA error a call of this library turned into a status.
 thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+// The CUDA device of this process's contexts (-1 until the first).
+std::atomic<int> g_process_device{-1};
 
 rte_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return RTE_OK;
@@ -770,6 +773,15 @@ rte_status rte_init_medium(rte_ctx** out, const rte_grid* g, const float* mua, c
     cudaGetLastError();
     delete c;
     return RTE_ERR_CUDA;
+  }
+  // One GPU per process: the first context fixes the device (the kernels'
+  // shared-memory limits are set once per process, on that device).
+  {
+    int expected = -1;
+    if (!g_process_device.compare_exchange_strong(expected, c->device) && expected != c->device) {
+      delete c;
+      return RTE_ERR_UNSUPPORTED;
+    }
   }
   c->plane = static_cast<size_t>(g->nx) * g->ny * g->M;
   c->ring_len = 2 * g->nx + 2 * g->ny;
