@@ -164,3 +164,20 @@ def test_header_is_plain_c():
         assert out.returncode == 0, out.stderr
     includes = [ln for ln in open(hdr) if ln.lstrip().startswith("#include")]
     assert all("<stddef.h>" in ln or "<stdint.h>" in ln for ln in includes), includes
+
+
+def test_binding_constants_match_the_header():
+    """Every integer constant the header defines (#define RTE_..., and the
+    rte_status codes) has the same value in the binding wherever the binding
+    names it; the precisions and flags must all be there."""
+    from paper_2202_09421_gb300 import binding
+    text = open(HEADER).read()
+    consts = {k: int(v) for k, v in re.findall(r"^#define\s+(RTE_\w+)\s+(\d+)\s*$", text, re.M)}
+    consts.update({k: int(v) for k, v in re.findall(r"^\s*(RTE_\w+)\s*=\s*(\d+)\s*,?", text, re.M)})
+    assert consts, "no constants parsed from the header"
+    for name, value in consts.items():
+        if hasattr(binding, name):
+            assert getattr(binding, name) == value, name
+    for name in consts:
+        if name.startswith(("RTE_PREC_", "RTE_FLAG_")):
+            assert hasattr(binding, name), name
