@@ -324,6 +324,14 @@ rte_status rte_host_fc_operator(int n, double h, double alpha, double beta, doub
 rte_status rte_host_fc_operator_parts(int n, double h, double alpha, double beta, int parts,
                                       double* D_out);
 rte_status rte_host_phase_matrix(int M, double g, double exponent, double* P_out);
+/* The segment operators of the decomposed operator as the tensor-core fused
+ * step (RTE_FLAG_TC_FUSED_STEP) takes them: for each part k, a hi tile then
+ * a lo tile of 16 rows (owned point i) x 32 tf32 values (box position p,
+ * the grid point lo - 2 + p), value (i, p) at i*32 + ((p/4) ^ (i%8))*4 + p%4
+ * (K-major, 128-byte swizzle); hi = tf32(D), lo = tf32(D - hi), zero outside
+ * the part's segment.  out: parts * 1024 floats.  Every part must own at
+ * most 16 points.  Errors: INVALID_ARG. */
+rte_status rte_host_segment_images(int n, double h, double alpha, double beta, int parts, float* out);
 /* The transpose of the linear part of the boundary map of eq. (RTE) that
  * rte_discrete_adjoint_gradient applies, for M ordinates and the refractive
  * indices n_in -> n_out.  Tables 0..3 are the faces (left, right, bottom,

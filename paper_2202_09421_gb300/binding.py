@@ -69,7 +69,7 @@ EXPORTS = ("rte_init_medium", "rte_set_medium", "rte_forward", "rte_detector_rea
            "rte_destroy", "rte_status_string", "rte_host_fc_operator", "rte_host_phase_matrix",
            "rte_set_kernel_timing", "rte_kernel_times", "rte_forward_static", "rte_forward_batch",
            "rte_graph_captures", "rte_set_pass_variant", "rte_last_cuda_error",
-           "rte_autotune", "rte_host_fc_operator_parts", "rte_discrete_adjoint_gradient",
+           "rte_autotune", "rte_host_fc_operator_parts", "rte_host_segment_images", "rte_discrete_adjoint_gradient",
            "rte_host_bc_transpose", "rte_inject_fault", "rte_photon_balance", "rte_adjoint_gradient_batch")
 
 _lib = None
@@ -101,6 +101,7 @@ def library() -> ctypes.CDLL:
         "rte_host_fc_operator": [c_int, c_double, c_double, c_double, P],
         "rte_host_phase_matrix": [c_int, c_double, c_double, P],
         "rte_host_fc_operator_parts": [c_int, c_double, c_double, c_double, c_int, P],
+        "rte_host_segment_images": [c_int, c_double, c_double, c_double, c_int, P],
         "rte_host_bc_transpose": [c_int, c_double, c_double, P, P],
         "rte_set_kernel_timing": [P, c_int],
         "rte_kernel_times": [P, POINTER(c_double), POINTER(c_longlong)],
@@ -308,6 +309,16 @@ def rte_host_fc_operator_parts(n: int, h: float, parts: int, alpha: float = 2.0,
     out = np.zeros((n, n), dtype=np.float64)
     _check(library().rte_host_fc_operator_parts(n, h, alpha, beta, int(parts), c_void_p(out.ctypes.data)),
            "rte_host_fc_operator_parts")
+    return out
+
+
+def rte_host_segment_images(n: int, h: float, parts: int, alpha: float = 2.0, beta: float = 55.0):
+    """The tensor-core fused step's segment-operator images (numpy float32
+    [parts][2][16][32]: hi and lo tiles in the swizzled K-major order)."""
+    import numpy as np
+    out = np.zeros((parts, 2, 16, 32), dtype=np.float32)
+    _check(library().rte_host_segment_images(n, h, alpha, beta, int(parts), c_void_p(out.ctypes.data)),
+           "rte_host_segment_images")
     return out
 
 

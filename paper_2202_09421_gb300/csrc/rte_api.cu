@@ -677,6 +677,23 @@ rte_status rte_host_fc_operator_parts(int n, double h, double alpha, double beta
   return RTE_OK;
 }
 
+rte_status rte_host_segment_images(int n, double h, double alpha, double beta, int parts, float* out) {
+  if (n < 16 || n > 4096 || !(h > 0) || !out || parts < 2) return RTE_ERR_INVALID_ARG;
+  std::vector<double> Dm;
+  if (!rte_setup::fc_derivative_matrix_parts(n, h, alpha, beta, parts, Dm)) return RTE_ERR_INVALID_ARG;
+  for (int k = 0; k < parts; ++k) {
+    int lo, hi, slo, shi;
+    rte_setup::part_range(n, parts, k, lo, hi, slo, shi);
+    if (hi - lo > rte_kern::kFusedOwnMax) return RTE_ERR_INVALID_ARG;
+  }
+  for (int k = 0; k < parts; ++k) {
+    int lo, hi, slo, shi;
+    rte_setup::part_range(n, parts, k, lo, hi, slo, shi);
+    rte_setup::tc_segment_image(Dm, n, lo, hi, slo, shi, out + static_cast<size_t>(k) * 2 * 16 * 32);
+  }
+  return RTE_OK;
+}
+
 rte_status rte_host_phase_matrix(int M, double g, double exponent, double* P_out) {
   if (M < 2 || !P_out || !(std::fabs(g) < 1.0)) return RTE_ERR_INVALID_ARG;
   std::vector<double> P;

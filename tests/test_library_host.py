@@ -181,3 +181,41 @@ def test_binding_constants_match_the_header():
     for name in consts:
         if name.startswith(("RTE_PREC_", "RTE_FLAG_")):
             assert hasattr(binding, name), name
+
+
+@pytest.mark.parametrize("n,parts", [(64, 4), (96, 6), (256, 16)])
+def test_host_segment_images_encode_the_decomposed_operator(B, n, parts):
+    """The segment-operator images of the tensor-core fused step, decoded
+    with the K-major 128-byte-swizzle layout of a tcgen05 operand (16-byte
+    group p/4 of row i stored at group (p/4) xor (i mod 8)): hi is a tf32
+    value (low 13 bits zero), hi + lo equals the decomposed operator's row of
+    owned point lo + i at grid point lo - 2 + p to the split's rounding, and
+    every entry outside the part's segment is zero."""
+    from oracle.fcgram import subdomain_segments
+    h = 1.0 / (n - 1)
+    D = B.rte_host_fc_operator_parts(n, h, parts)
+    img = B.rte_host_segment_images(n, h, parts)
+    scale = np.abs(D).max()
+    i_idx = np.arange(16)[:, None]
+    p_idx = np.arange(32)[None, :]
+    pos = ((p_idx >> 2) ^ (i_idx & 7)) * 4 + (p_idx & 3)          # [16][32] storage column
+    for k, (lo, hi, slo, shi) in enumerate(subdomain_segments(n, parts)):
+        hi_v = np.take_along_axis(img[k, 0], pos, axis=1).astype(np.float64)
+        lo_v = np.take_along_axis(img[k, 1], pos, axis=1).astype(np.float64)
+        assert np.all(img[k, 0].view(np.uint32) & 0x1FFF == 0)     # tf32-representable
+        want = np.zeros((16, 32))
+        for i in range(hi - lo):
+            for p in range(32):
+                x = lo - 2 + p
+                if slo <= x < shi:
+                    want[i, p] = D[lo + i, x]
+        assert np.all((hi_v + lo_v)[want == 0] == 0)
+        assert np.abs(hi_v + lo_v - want).max() <= 2.0 ** -21 * scale
+        assert np.abs(hi_v - want).max() > 0 or np.abs(want).max() == 0   # lo carries the rest
+
+
+def test_host_segment_images_rejects_long_parts(B):
+    """Parts owning more than 16 points have no image (the fused step
+    does not take them)."""
+    with pytest.raises(B.RTEError):
+        B.rte_host_segment_images(96, 1.0 / 95, 3)
